@@ -1,0 +1,305 @@
+#!/usr/bin/env python3
+"""Benchmark of the VQE hot path on GB300: batched energy + adjoint-gradient evaluations.
+
+Workload (one "step"): 4096 independent hardware-efficient-ansatz instances, n ~ U{4..12}
+qubits, L ~ U{2..8} layers of RY/RZ on every qubit plus a CNOT ladder, Pauli sums of
+T ~ U{50..500} Z-heavy terms; each step evaluates every instance's energy and full adjoint
+gradient in complex128 in one persistent launch replayed from a CUDA graph.  Inputs are
+seeded and synthetic.  With torchrun (N > 1) every rank runs its own 4096 instances (weak
+scaling, no collective on the data path).
+
+Prints one JSON line (rank 0).  ``--impl reference`` times the plain CPU oracle instead.
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "VQE energy+grad evals/s (batched, 4096 HEA instances n=4..12, complex128)"
+UNIT = "evals/s"
+FP64_PEAK_TFLOPS = 2 * 2 * 152 * 2.070e9 / 1e12  # 2 DFMA/clk/SM x 2 flop x 152 SMs x 2.07 GHz
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--instances", type=int, default=4096)
+    ap.add_argument("--seed", type=int, default=1002)
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def config(args, world):
+    return {"workload": f"hea_batch_{args.instances}_n4-12_L2-8_T50-500",
+            "instances_per_gpu": args.instances, "qubits": "4-12", "layers": "2-8",
+            "terms": "50-500 (70% I/Z-only, weight<=4)", "seed": args.seed,
+            "ansatz": "RY+RZ on all qubits + CNOT ladder per layer",
+            "l2": "flushed between timed steps (256 MiB write)",
+            "parallelism": f"replicas{world}"}
+
+
+def algorithmic_fp64_flops(insts):
+    """FP64 flops (FMA = 2) of one energy + adjoint-gradient pass, counted from the kernel's
+    arithmetic: lifting rotations 12 flop per pair (6 DFMA), gradient inner product 7 flop per
+    pair (1 DMUL + 3 DFMA) plus 1 DADD, H 8 flop per pair, group tables 4 flop per amplitude
+    (real or imaginary) or 8 (complex), energy 4 flop per amplitude."""
+    from paper_2601_09951_gb300 import svqe
+    from paper_2601_09951_gb300 import workloads as W
+    total = 0.0
+    for inst in insts:
+        c = inst["circuit"]
+        n = int(c["n"])
+        N = 1 << n
+        for t, p in zip(c["types"], c["params"]):
+            t = int(t)
+            pairs = {W.SINGLE_EXC: N // 4, W.DOUBLE_EXC: N // 16}.get(t, N // 2)
+            if t in (W.RX, W.RY, W.RZ, W.SINGLE_EXC, W.DOUBLE_EXC):
+                total += pairs * (12 + 24 + (8 if p >= 0 else 0))
+            elif t == W.H:
+                total += pairs * (8 + 16)
+        _, _, cls, _, _ = svqe.ham_lower(inst["ham"], n, 12)
+        total += N * (4 * np.sum(cls < 2) + 8 * np.sum(cls == 2) + 4)
+    return total
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms while running."""
+
+    FIELDS = ("index,uuid,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, uuid=None):
+        self.uuid = uuid
+        self.file = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=self.file, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        self.file.flush()
+        self.file.seek(0)
+        rows = [r.split(", ") for r in self.file.read().splitlines() if r.strip()]
+        os.unlink(self.file.name)
+        if self.uuid:
+            mine = [r for r in rows if len(r) > 1 and r[1].strip() == self.uuid]
+            rows = mine or rows
+        sm = [float(r[2]) for r in rows if len(r) >= 10 and r[2].strip().replace(".", "").isdigit()]
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        reasons = set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            for k, name in enumerate(names):
+                if len(r) > 6 + k and r[6 + k].strip() == "Active":
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": float(rows[0][3]),
+                "samples": len(sm), "reasons": sorted(reasons),
+                "power_w_max": max(float(r[4]) for r in rows if r[4].strip()[0].isdigit())}
+
+
+def cpu_baseline(args, seconds, first_index=0):
+    """The oracle (parameter-shift gradient, OpenMP over shifted evaluations on all host
+    cores) on consecutive instances of the same seeded workload until `seconds` elapse."""
+    import oracle
+    from paper_2601_09951_gb300 import workloads as W
+    cores = os.cpu_count() or 1
+    oracle.set_threads(cores)
+    done, t0 = 0, time.perf_counter()
+    i = first_index
+    while time.perf_counter() - t0 < seconds:
+        inst = W.hea_batch(args.instances, seed=args.seed, indices=[i % args.instances])[0]
+        oracle.energy_grad(inst)
+        done += 1
+        i += 1
+    dt = time.perf_counter() - t0
+    return {"value": done / dt, "unit": UNIT, "cores": oracle.get_threads(), "kind": "oracle",
+            "sample": f"instances {first_index}..{i - 1} of the same seeded workload "
+                      f"({done} energy+gradient evaluations, parameter-shift, {dt:.1f} s)"}
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    import oracle
+    from paper_2601_09951_gb300 import workloads as W
+    cores = os.cpu_count() or 1
+    oracle.set_threads(cores)
+    per_step = 4
+    times = []
+    for s in range(args.warmup + args.steps):
+        idx = [(s * per_step + k) % args.instances for k in range(per_step)]
+        insts = W.hea_batch(args.instances, seed=args.seed, indices=idx)
+        t0 = time.perf_counter()
+        for inst in insts:
+            oracle.energy_grad(inst)
+        if s >= args.warmup:
+            times.append(time.perf_counter() - t0)
+    total = sum(times)
+    value = per_step * len(times) / total
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * total / len(times), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": config(args, world),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": oracle.get_threads(),
+                             "kind": "oracle",
+                             "sample": f"{per_step} instances per step, consecutive seeded "
+                                       f"indices, parameter-shift gradient on {cores} cores"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    rank, world, local = dist_env()
+    if args.impl == "reference":
+        run_reference(args)
+        return
+    import torch
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    from paper_2601_09951_gb300 import build as libbuild
+    libbuild.build()
+    from paper_2601_09951_gb300 import svqe
+    from paper_2601_09951_gb300 import workloads as W
+
+    idx = list(range(rank * args.instances, (rank + 1) * args.instances))
+    insts = W.hea_batch(args.instances * world, seed=args.seed, indices=idx)
+    stream = torch.cuda.Stream()
+    batch = svqe.Batch(insts, stream=stream.cuda_stream)
+    theta_h = batch.theta_of(insts)
+    P = batch.n_params
+    theta = torch.tensor(theta_h, dtype=torch.float64, device="cuda")
+    energy = torch.empty(len(insts), dtype=torch.float64, device="cuda")
+    grad = torch.empty(P, dtype=torch.float64, device="cuda")
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            batch.run_dev(theta.data_ptr(), energy.data_ptr(), grad.data_ptr())
+        torch.cuda.synchronize()
+        starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+        ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+        uuid = None
+        try:
+            uuid = "GPU-" + str(torch.cuda.get_device_properties(local).uuid)
+        except Exception:
+            pass
+        with ClockSampler(uuid) as clk:
+            barrier()
+            torch.cuda.synchronize()
+            w0 = time.perf_counter()
+            for s in range(args.steps):
+                flush.zero_()
+                starts[s].record(stream)
+                batch.run_dev(theta.data_ptr(), energy.data_ptr(), grad.data_ptr())
+                ends[s].record(stream)
+            torch.cuda.synchronize()
+            barrier()
+            wall = time.perf_counter() - w0
+        step_ms = [a.elapsed_time(b) for a, b in zip(starts, ends)]
+        dev_s = sum(step_ms) / 1e3
+        clocks = clk.summary()
+
+        # End to end through the public API with pinned host buffers: H2D theta, the launch,
+        # D2H energies and gradients, every step.
+        th_h = torch.tensor(theta_h, dtype=torch.float64).pin_memory()
+        e_h = torch.empty(len(insts), dtype=torch.float64).pin_memory()
+        g_h = torch.empty(max(P, 1), dtype=torch.float64).pin_memory()
+        for _ in range(2):
+            batch.run_ptr(th_h.data_ptr(), e_h.data_ptr(), g_h.data_ptr())
+        barrier()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for s in range(args.steps):
+            batch.run_ptr(th_h.data_ptr(), e_h.data_ptr(), g_h.data_ptr())
+        torch.cuda.synchronize()
+        barrier()
+        e2e_s = time.perf_counter() - t0
+
+    times = torch.tensor([dev_s, e2e_s, wall], dtype=torch.float64, device="cuda")
+    if dist is not None:
+        dist.all_reduce(times, op=dist.ReduceOp.MAX)
+    dev_s, e2e_s, wall = times.tolist()
+    n_total = args.instances * world
+    value = n_total * args.steps / dev_s
+    if rank != 0:
+        if dist is not None:
+            dist.destroy_process_group()
+        return
+    flops = algorithmic_fp64_flops(insts)
+    kernel_s = dev_s / args.steps
+    achieved = flops / kernel_s / 1e12
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * dev_s / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic (seeded generator, shapes of the batched workload)",
+        "config": config(args, world),
+        "e2e": {"value": n_total * args.steps / e2e_s, "unit": UNIT,
+                "h2d_bytes_per_step": int(8 * P), "d2h_bytes_per_step": int(8 * (P + len(insts)))},
+        "gpu_launches": args.steps,
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS,
+                     "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,
+                     "kernel": "k_batch", "what": "FP64 pipe (2 DFMA/clk/SM x 152 SMs x "
+                     "2.07 GHz); algorithmic FP64 flops per launch / mean launch time",
+                     "flops_per_launch": flops},
+        "clocks": clocks,
+        "wall_s_incl_l2_flush": wall,
+    }
+    if world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(args, args.cpu_seconds)
+    print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,218 @@
+/*
+ * svqe.h -- C ABI of libsvqe.so, the GB300 (sm_103a) state-vector VQE hot path.
+ *
+ * The paper (Malarchick & Steed, "Parallelizing the Variational Quantum Eigensolver", 2026)
+ * poses the problem as: for each Hamiltonian H(d) (Sec. 2.2), prepare |psi(theta)> =
+ * U(theta)|HF> (Sec. 3.3, Eq. 4-5), evaluate E(theta) = <psi|H|psi> (Sec. 3.1, Eq. 2) and
+ * its gradient, and update theta (Algorithm 1; Sec. 3.4).  This header exposes exactly those
+ * steps over complex128 amplitudes on one GPU.
+ *
+ * Conventions shared by every call
+ *   - Amplitudes are complex128, stored interleaved (re, im) as 16-byte pairs; a state of
+ *     n qubits has 2^n amplitudes (Table 3: 2^n x 16 bytes).
+ *   - Qubit q is bit (n-1-q) of a basis index (qubit 0 is the most significant bit), so the
+ *     Hartree-Fock state |1100> of Eq. 4 has basis index 12.
+ *   - A Pauli string is a pair of masks over basis-index bits: x has the bits whose factor is
+ *     X or Y, z the bits whose factor is Z or Y; the string is i^{popc(x&z)} X^x Z^z
+ *     (Y = iXZ).  Coefficients are real (Sec. 3.2, Eq. 3 after Jordan-Wigner).
+ *   - Gates: RX/RY/RZ(t) = exp(-i t/2 X/Y/Z); CNOT(control, target); CZ; X; H;
+ *     SingleExcitation(t) on wires (a, b) rotates span{|01>, |10>} by t/2 and
+ *     DoubleExcitation(t) on (a, b, c, d) rotates span{|0011>, |1100>} by t/2:
+ *       |lo> -> cos(t/2)|lo> + sin(t/2)|hi>,  |hi> -> cos(t/2)|hi> - sin(t/2)|lo>
+ *     (Eq. 5 read as exp(-t/2 (A - A^dag)), A = a0^dag a1^dag a2 a3 under Jordan-Wigner).
+ *
+ * Ownership: the caller owns every array it passes; the library copies what it keeps.
+ * Handles (sv_ctx, sv_ham, sv_batch, sv_server) belong to the library until freed.
+ * Pointers named *_dev are device pointers; all other array pointers are host pointers.
+ *
+ * Streams: every call is ordered on the stream of its context or batch.  Calls that return
+ * host values (energies, gradients, states) synchronise that stream before returning.
+ *
+ * Errors: every call returns sv_status and never aborts the process.  SV_EINVAL reports a
+ * malformed argument (bad wire, duplicate wire, qubit count outside [1, 31], mask bit >= n,
+ * parameter index out of range, NULL pointer).  SV_ECUDA reports a CUDA failure; the handle
+ * that saw it is then unusable ("sticky") and must be destroyed.  sv_last_error() gives the
+ * calling thread's most recent message.
+ *
+ * Threading: a handle may be used by one host thread at a time.  Different handles may be
+ * used concurrently from different threads.
+ */
+#ifndef SVQE_H
+#define SVQE_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  SV_OK = 0,
+  SV_EINVAL = 1,        /* malformed argument */
+  SV_ENOMEM = 2,        /* device or host allocation failed, or an HBM budget is exceeded */
+  SV_ECUDA = 3,         /* a CUDA call failed; the handle is now unusable */
+  SV_ETIMEOUT = 4,      /* a bounded wait ran out */
+  SV_EUNSUPPORTED = 5,  /* valid request this build does not implement */
+  SV_EBUSY = 6          /* result not ready yet (serving poll) */
+} sv_status;
+
+/* Gate codes (the `type` field of sv_gate). */
+enum {
+  SV_GATE_X = 0,
+  SV_GATE_H = 1,
+  SV_GATE_RX = 2,
+  SV_GATE_RY = 3,
+  SV_GATE_RZ = 4,
+  SV_GATE_CNOT = 5,
+  SV_GATE_SINGLE_EXC = 6,
+  SV_GATE_DOUBLE_EXC = 7,
+  SV_GATE_CZ = 8
+};
+
+/* One gate record, 32 bytes.  wires: the first 1, 2 or 4 entries are used (others ignored);
+ * param: index into theta, or -1 to use fixed_angle.  X, H, CNOT and CZ ignore the angle. */
+typedef struct {
+  int32_t type;
+  int32_t wires[4];
+  int32_t param;
+  double fixed_angle;
+} sv_gate;
+
+/* A circuit U = U_{n_gates-1} ... U_0 (gates applied in array order) with n_params angles. */
+typedef struct {
+  int32_t n_qubits;
+  int32_t n_gates;
+  int32_t n_params;
+  const sv_gate* gates;
+} sv_circuit;
+
+/* H = sum_t coeff[t] * P(x_mask[t], z_mask[t])  (Sec. 3.2). */
+typedef struct {
+  int32_t n_qubits;
+  int32_t n_terms;
+  const uint64_t* x_mask;
+  const uint64_t* z_mask;
+  const double* coeff;
+} sv_paulisum;
+
+typedef struct sv_ctx sv_ctx;        /* one n-qubit state: psi and lambda buffers + stream */
+typedef struct sv_ham sv_ham;        /* device-resident grouped Pauli sum                  */
+typedef struct sv_batch sv_batch;    /* many small instances, run by one persistent kernel */
+typedef struct sv_server sv_server;  /* continuous-batching request loop                   */
+
+/* ---------------------------------------------------------------- library information */
+
+/* Human-readable name of a status code (static string). */
+const char* sv_status_str(sv_status s);
+/* The calling thread's most recent error message ("" if none); valid until its next call. */
+const char* sv_last_error(void);
+/* ABI version, currently 1. */
+int32_t sv_abi_version(void);
+/* Bytes of one n-qubit complex128 state, 2^n * 16 (Table 3); 0 if n is outside [0, 62]. */
+uint64_t sv_state_bytes(int32_t n_qubits);
+/* Device bytes a context of n qubits allocates: two state buffers (psi, lambda) plus
+ * reduction scratch.  At most three state-sized buffers are ever used (31 qubits fit). */
+uint64_t sv_ctx_device_bytes(int32_t n_qubits);
+
+/* ---------------------------------------------------------------- contexts */
+
+/* Create a context for n_qubits in [1, 31].  cuda_stream is a cudaStream_t to order work on,
+ * or NULL for a stream the context creates and owns.  Allocates psi and lambda (2 x 2^n x 16
+ * bytes) and scratch on the current device; SV_ENOMEM if that fails. */
+sv_status sv_create(sv_ctx** out, int32_t n_qubits, void* cuda_stream);
+/* Free a context and everything it allocated (NULL is accepted). */
+sv_status sv_destroy(sv_ctx* ctx);
+
+/* ---------------------------------------------------------------- Hamiltonians */
+
+/* Copy a Pauli sum to the device, grouped by X-flip mask: terms sharing x are one group
+ * whose phase-and-sign function f_g(i) = sum_{t in g} c_t i^{popc(x&z_t)} (-1)^{popc(z_t&i)}
+ * is tabulated over the bits its z masks touch, so each group reads psi once per amplitude.
+ * Mask bits >= n_qubits are SV_EINVAL.  The handle may be used with any context of the same
+ * qubit count on the same device. */
+sv_status sv_ham_upload(sv_ctx* ctx, const sv_paulisum* h, sv_ham** out);
+sv_status sv_ham_free(sv_ham* h);
+/* Number of X-mask groups and device bytes of a handle (either pointer may be NULL). */
+sv_status sv_ham_info(const sv_ham* h, int32_t* n_groups, uint64_t* device_bytes);
+
+/* Host-only inspection of the grouping sv_ham_upload performs (no device work): with
+ * kmax = largest number of z-bits a group table may span (a single term wider than kmax
+ * gets a table of its own z-weight), fills n_groups and n_table and,
+ * when the array pointers are non-NULL (sized from a first call with NULL arrays), the
+ * groups (x, zu, cls, toff) and the tables as interleaved (re, im) doubles.  Group g maps
+ * (H psi)[k] += table[toff_g + pext(k, zu_g)] * psi[k ^ x_g]; cls is 0 (real table),
+ * 1 (imaginary) or 2 (complex). */
+sv_status sv_ham_lower(const sv_paulisum* h, int32_t kmax, int32_t* n_groups, int64_t* n_table,
+                       uint64_t* x, uint64_t* zu, int32_t* cls, int64_t* toff, double* table);
+
+/* ---------------------------------------------------------------- one state */
+
+/* psi = |basis_index> (Eq. 4); also records it as the context's reference state, the
+ * starting point of sv_adjoint_grad and vqe_step.  basis_index must be < 2^n. */
+sv_status sv_init_reference(sv_ctx* ctx, uint64_t basis_index);
+/* psi <- U(theta) psi, gates in order.  theta: host array of circuit->n_params angles. */
+sv_status sv_apply_circuit(sv_ctx* ctx, const sv_circuit* circuit, const double* theta);
+/* *energy_out = <psi|H|psi> for the context's current psi (Eq. 2). */
+sv_status sv_expval_paulisum(sv_ctx* ctx, const sv_ham* h, double* energy_out);
+/* Energy and gradient of E(theta) = <ref|U^dag H U|ref>, with |ref> the reference state of the
+ * last sv_init_reference (|0> if none).  Forward pass, lambda = H psi, then the adjoint sweep
+ * over gates in reverse: g_p += 2 Im<lambda|G_l|psi> for each gate l with parameter p, then
+ * psi <- U_l^dag psi and lambda <- U_l^dag lambda.  Uses psi and lambda only.  energy_out:
+ * host double; grad_out: host array of n_params (gates sharing a parameter are summed). */
+sv_status sv_adjoint_grad(sv_ctx* ctx, const sv_circuit* circuit, const double* theta,
+                          const sv_ham* h, double* energy_out, double* grad_out);
+/* As sv_adjoint_grad with device pointers (theta_dev: n_params doubles; energy_dev: 1
+ * double; grad_dev: n_params doubles).  Stream-ordered; does not synchronise. */
+sv_status sv_adjoint_grad_dev(sv_ctx* ctx, const sv_circuit* circuit, const double* theta_dev,
+                              const sv_ham* h, double* energy_dev, double* grad_dev);
+/* n_steps of gradient descent theta <- theta - lr * dE/dtheta from the reference state
+ * (Algorithm 1's inner loop with a fixed step).  theta_inout: host, n_params, updated in
+ * place.  energy_out: host array of n_steps (E before each update) or NULL. */
+sv_status vqe_step(sv_ctx* ctx, const sv_circuit* circuit, const sv_ham* h, double* theta_inout,
+                   double lr, int32_t n_steps, double* energy_out);
+/* Copy psi to / from host memory (2^n interleaved complex128). */
+sv_status sv_get_state(sv_ctx* ctx, void* host_out);
+sv_status sv_set_state(sv_ctx* ctx, const void* host_in);
+/* Device address of psi (valid until sv_destroy). */
+sv_status sv_state_device_ptr(sv_ctx* ctx, void** psi_dev);
+
+/* ---------------------------------------------------------------- batches */
+
+/* One instance of a batch: its circuit, its Hamiltonian and its reference basis index.
+ * circuit.n_qubits must equal ham.n_qubits and lie in [1, SV_BATCH_MAX_QUBITS]. */
+typedef struct {
+  sv_circuit circuit;
+  sv_paulisum ham;
+  uint64_t ref;
+} sv_instance;
+
+#define SV_BATCH_MAX_QUBITS 12
+
+/* Compile and upload n instances (Sec. 4.1, Eq. 7: independent problems) for the persistent
+ * batched kernel, which keeps each instance's psi and lambda in shared memory.  Theta and
+ * gradients of all instances are concatenated in instance order (offsets = prefix sums of
+ * n_params).  cuda_stream: NULL for an owned stream. */
+sv_status sv_batch_create(const sv_instance* inst, int32_t n, void* cuda_stream,
+                          sv_batch** out);
+sv_status sv_batch_free(sv_batch* b);
+/* Sizes: instances, total parameters. */
+sv_status sv_batch_info(const sv_batch* b, int32_t* n_instances, int64_t* n_params_total);
+/* Energy and adjoint gradient of every instance, host buffers: theta (n_params_total) is
+ * copied in, energy (n) and grad (n_params_total) are copied out; synchronises. */
+sv_status sv_batch_run(sv_batch* b, const double* theta, double* energy, double* grad);
+/* The same on device buffers; one persistent launch, replayed from a CUDA graph captured on
+ * the first call for these pointers.  Stream-ordered; does not synchronise. */
+sv_status sv_batch_run_dev(sv_batch* b, const double* theta_dev, double* energy_dev,
+                           double* grad_dev);
+/* n_steps of gradient descent on every instance inside one persistent launch:
+ * theta_dev is updated in place; energy_traj_dev (n_steps x n, step-major) receives E before
+ * each update, or may be NULL.  Stream-ordered. */
+sv_status sv_batch_vqe_dev(sv_batch* b, double* theta_dev, double lr, int32_t n_steps,
+                           double* energy_traj_dev);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SVQE_H */

@@ -167,7 +167,7 @@ static inline void nsum_add(nsum* a, double v) {
 }
 static inline double nsum_get(const nsum* a) { return a->s + a->c; }
 
-static int popcount64(uint64_t v) { int k = 0; while (v) { v &= v - 1; ++k; } return k; }
+static int popcount64(uint64_t v) { return __builtin_popcountll(v); }
 
 /* <psi|P|psi> for one Pauli string, summed over i of conj(psi[i^x]) * (P|i> coefficient) *
  * psi[i].  Sec. 3.2: H is a real-weighted sum of Pauli strings. */

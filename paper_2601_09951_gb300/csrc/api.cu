@@ -1,0 +1,685 @@
+// api.cu -- the C ABI of libsvqe.so (include/svqe.h): contexts, Hamiltonians, the single-state
+// path and batches.  Host code only; kernels live in k_state.cu and k_batch.cu.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <numeric>
+#include <vector>
+
+#include "../../include/svqe.h"
+#include "host_compile.h"
+#include "launch.h"
+#include "svqe_types.h"
+
+using namespace svqe;
+
+// ------------------------------------------------------------------------------ handles
+struct sv_ctx {
+  int n = 0;
+  uint64_t N = 0;
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  bool sticky = false;
+  uint64_t ref = 0;
+  double2* psi = nullptr;
+  double2* lam = nullptr;
+  double* epart = nullptr;    // kRedBlocks energy partials
+  double* scal = nullptr;     // [0] energy
+  // circuit-sized buffers, grown on demand
+  DOp* ops = nullptr;
+  Rot* coef = nullptr;
+  double* contrib = nullptr;
+  size_t ops_cap = 0, coef_cap = 0, contrib_cap = 0;
+  double* gpart = nullptr;    // n_ops x kRedBlocks gradient partials
+  size_t gpart_cap = 0;
+  double* theta = nullptr;
+  double* grad = nullptr;
+  size_t theta_cap = 0, grad_cap = 0;
+  double* etraj = nullptr;
+  size_t etraj_cap = 0;
+};
+
+struct sv_ham {
+  int n = 0;
+  int device = 0;
+  int n_groups = 0;
+  DGroup* groups = nullptr;
+  double2* tables = nullptr;
+  uint64_t bytes = 0;
+  double l1 = 0.0;
+};
+
+struct sv_batch {
+  int n_inst = 0;
+  int nmax = 0;
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  bool sticky = false;
+  int64_t total_params = 0;
+  int64_t total_ops = 0;
+  int grid = 0;
+  size_t smem = 0;
+  BInst* inst = nullptr;
+  int32_t* order = nullptr;
+  DOp* ops = nullptr;
+  DGroup* groups = nullptr;
+  double2* tables = nullptr;
+  Rot* coef = nullptr;
+  double* contrib = nullptr;
+  int* counter = nullptr;
+  double* theta = nullptr;   // owned buffers for the host-pointer entry point
+  double* energy = nullptr;
+  double* grad = nullptr;
+  // CUDA graph of [counter reset, persistent kernel] for one set of device pointers
+  cudaGraphExec_t exec = nullptr;
+  const void* key[3] = {nullptr, nullptr, nullptr};
+};
+
+// ------------------------------------------------------------------------------ helpers
+#define SV_CUDA(call, handle)                                                        \
+  do {                                                                               \
+    cudaError_t e_ = (call);                                                         \
+    if (e_ != cudaSuccess) {                                                         \
+      set_error("%s: %s (%s:%d)", #call, cudaGetErrorString(e_), __FILE__, __LINE__); \
+      if (handle) (handle)->sticky = true;                                           \
+      return SV_ECUDA;                                                               \
+    }                                                                                \
+  } while (0)
+
+#define SV_CHECK_STICKY(h)                                                  \
+  do {                                                                      \
+    if ((h)->sticky) {                                                      \
+      set_error("handle is unusable after an earlier CUDA error");          \
+      return SV_ECUDA;                                                      \
+    }                                                                       \
+  } while (0)
+
+template <class T>
+static cudaError_t grow(T*& p, size_t& cap, size_t need) {
+  if (need <= cap && p) return cudaSuccess;
+  if (p) cudaFree(p);
+  p = nullptr;
+  cap = 0;
+  size_t c = std::max<size_t>(need, 64);
+  cudaError_t e = cudaMalloc((void**)&p, c * sizeof(T));
+  if (e == cudaSuccess) cap = c;
+  return e;
+}
+
+extern "C" {
+
+const char* sv_status_str(sv_status s) {
+  switch (s) {
+    case SV_OK: return "SV_OK";
+    case SV_EINVAL: return "SV_EINVAL";
+    case SV_ENOMEM: return "SV_ENOMEM";
+    case SV_ECUDA: return "SV_ECUDA";
+    case SV_ETIMEOUT: return "SV_ETIMEOUT";
+    case SV_EUNSUPPORTED: return "SV_EUNSUPPORTED";
+    case SV_EBUSY: return "SV_EBUSY";
+    default: return "SV_UNKNOWN";
+  }
+}
+
+const char* sv_last_error(void) { return last_error(); }
+int32_t sv_abi_version(void) { return 1; }
+
+uint64_t sv_state_bytes(int32_t n) {
+  if (n < 0 || n > 62) return 0;
+  return (uint64_t)16 << n;
+}
+
+uint64_t sv_ctx_device_bytes(int32_t n) {
+  if (n < 1 || n > 31) return 0;
+  return 2 * sv_state_bytes(n) + (uint64_t)(kRedBlocks + 8) * sizeof(double);
+}
+
+// ------------------------------------------------------------------------------ contexts
+sv_status sv_create(sv_ctx** out, int32_t n, void* stream) {
+  clear_error();
+  if (!out) { set_error("out is NULL"); return SV_EINVAL; }
+  *out = nullptr;
+  if (n < 1 || n > 31) { set_error("n_qubits %d outside [1, 31]", n); return SV_EINVAL; }
+  sv_ctx* c = new (std::nothrow) sv_ctx();
+  if (!c) { set_error("host allocation failed"); return SV_ENOMEM; }
+  c->n = n;
+  c->N = 1ull << n;
+  cudaGetDevice(&c->device);
+  if (stream) {
+    c->stream = (cudaStream_t)stream;
+  } else {
+    cudaError_t e = cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking);
+    if (e != cudaSuccess) {
+      set_error("cudaStreamCreate: %s", cudaGetErrorString(e));
+      delete c;
+      return SV_ECUDA;
+    }
+    c->own_stream = true;
+  }
+  const size_t sb = sv_state_bytes(n);
+  if (cudaMalloc((void**)&c->psi, sb) != cudaSuccess ||
+      cudaMalloc((void**)&c->lam, sb) != cudaSuccess ||
+      cudaMalloc((void**)&c->epart, kRedBlocks * sizeof(double)) != cudaSuccess ||
+      cudaMalloc((void**)&c->scal, 8 * sizeof(double)) != cudaSuccess) {
+    cudaGetLastError();
+    set_error("device allocation of %llu bytes for %d qubits failed",
+              (unsigned long long)sv_ctx_device_bytes(n), n);
+    sv_destroy(c);
+    return SV_ENOMEM;
+  }
+  c->ref = 0;
+  if (launch_init_basis(c->psi, n, 0, c->stream) != cudaSuccess) {
+    set_error("init kernel launch failed");
+    sv_destroy(c);
+    return SV_ECUDA;
+  }
+  *out = c;
+  return SV_OK;
+}
+
+sv_status sv_destroy(sv_ctx* c) {
+  if (!c) return SV_OK;
+  cudaSetDevice(c->device);
+  if (c->stream) cudaStreamSynchronize(c->stream);
+  cudaFree(c->psi);
+  cudaFree(c->lam);
+  cudaFree(c->epart);
+  cudaFree(c->scal);
+  cudaFree(c->ops);
+  cudaFree(c->coef);
+  cudaFree(c->contrib);
+  cudaFree(c->gpart);
+  cudaFree(c->theta);
+  cudaFree(c->grad);
+  cudaFree(c->etraj);
+  if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
+  cudaGetLastError();
+  delete c;
+  return SV_OK;
+}
+
+// ------------------------------------------------------------------------------ Hamiltonians
+static constexpr int kTableBitsState = 14;  // largest per-group table, single-state path
+
+sv_status sv_ham_upload(sv_ctx* c, const sv_paulisum* h, sv_ham** out) {
+  clear_error();
+  if (!c || !out) { set_error("NULL argument"); return SV_EINVAL; }
+  *out = nullptr;
+  SV_CHECK_STICKY(c);
+  HostHam hh;
+  sv_status st = lower_ham(h, c->n, kTableBitsState, hh);
+  if (st != SV_OK) return st;
+  sv_ham* H = new (std::nothrow) sv_ham();
+  if (!H) { set_error("host allocation failed"); return SV_ENOMEM; }
+  H->n = c->n;
+  H->device = c->device;
+  H->n_groups = (int)hh.groups.size();
+  H->l1 = hh.l1;
+  const size_t gb = std::max<size_t>(1, hh.groups.size()) * sizeof(DGroup);
+  const size_t tb = std::max<size_t>(1, hh.tables.size()) * sizeof(double2);
+  H->bytes = gb + tb;
+  if (cudaMalloc((void**)&H->groups, gb) != cudaSuccess ||
+      cudaMalloc((void**)&H->tables, tb) != cudaSuccess) {
+    cudaGetLastError();
+    sv_ham_free(H);
+    set_error("device allocation of %llu bytes for a Hamiltonian failed",
+              (unsigned long long)(gb + tb));
+    return SV_ENOMEM;
+  }
+  if (!hh.groups.empty())
+    SV_CUDA(cudaMemcpyAsync(H->groups, hh.groups.data(), hh.groups.size() * sizeof(DGroup),
+                            cudaMemcpyHostToDevice, c->stream), c);
+  if (!hh.tables.empty())
+    SV_CUDA(cudaMemcpyAsync(H->tables, hh.tables.data(), hh.tables.size() * sizeof(double2),
+                            cudaMemcpyHostToDevice, c->stream), c);
+  SV_CUDA(cudaStreamSynchronize(c->stream), c);
+  *out = H;
+  return SV_OK;
+}
+
+sv_status sv_ham_free(sv_ham* H) {
+  if (!H) return SV_OK;
+  cudaSetDevice(H->device);
+  cudaFree(H->groups);
+  cudaFree(H->tables);
+  cudaGetLastError();
+  delete H;
+  return SV_OK;
+}
+
+sv_status sv_ham_info(const sv_ham* H, int32_t* n_groups, uint64_t* bytes) {
+  if (!H) { set_error("NULL handle"); return SV_EINVAL; }
+  if (n_groups) *n_groups = H->n_groups;
+  if (bytes) *bytes = H->bytes;
+  return SV_OK;
+}
+
+sv_status sv_ham_lower(const sv_paulisum* h, int32_t kmax, int32_t* n_groups, int64_t* n_table,
+                       uint64_t* x, uint64_t* zu, int32_t* cls, int64_t* toff, double* table) {
+  clear_error();
+  if (!h || !n_groups || !n_table) { set_error("NULL argument"); return SV_EINVAL; }
+  HostHam hh;
+  sv_status st = lower_ham(h, 0, kmax, hh);
+  if (st != SV_OK) return st;
+  const int cap_g = *n_groups;
+  const int64_t cap_t = *n_table;
+  *n_groups = (int32_t)hh.groups.size();
+  *n_table = (int64_t)hh.tables.size();
+  if (x || zu || cls || toff || table) {
+    if (cap_g < (int)hh.groups.size() || cap_t < (int64_t)hh.tables.size()) {
+      set_error("output arrays too small (%d groups, %lld table entries needed)",
+                (int)hh.groups.size(), (long long)hh.tables.size());
+      return SV_EINVAL;
+    }
+    for (size_t g = 0; g < hh.groups.size(); ++g) {
+      if (x) x[g] = hh.groups[g].x;
+      if (zu) zu[g] = hh.groups[g].zu;
+      if (cls) cls[g] = hh.groups[g].cls;
+      if (toff) toff[g] = hh.groups[g].toff;
+    }
+    if (table)
+      for (size_t t = 0; t < hh.tables.size(); ++t) {
+        table[2 * t] = hh.tables[t].x;
+        table[2 * t + 1] = hh.tables[t].y;
+      }
+  }
+  return SV_OK;
+}
+
+// ------------------------------------------------------------------------------ one state
+sv_status sv_init_reference(sv_ctx* c, uint64_t b) {
+  clear_error();
+  if (!c) { set_error("NULL handle"); return SV_EINVAL; }
+  SV_CHECK_STICKY(c);
+  if (b >= c->N) { set_error("basis index %llu >= 2^%d", (unsigned long long)b, c->n); return SV_EINVAL; }
+  c->ref = b;
+  SV_CUDA(launch_init_basis(c->psi, c->n, b, c->stream), c);
+  return SV_OK;
+}
+
+// Upload a lowered circuit's ops and make sure every circuit-sized buffer fits.
+static sv_status stage_circuit(sv_ctx* c, const HostCircuit& hc) {
+  const size_t n_ops = hc.ops.size();
+  SV_CUDA(grow(c->ops, c->ops_cap, n_ops), c);
+  SV_CUDA(grow(c->coef, c->coef_cap, n_ops), c);
+  SV_CUDA(grow(c->contrib, c->contrib_cap, n_ops), c);
+  SV_CUDA(grow(c->gpart, c->gpart_cap, std::max<size_t>(1, n_ops) * kRedBlocks), c);
+  SV_CUDA(grow(c->theta, c->theta_cap, (size_t)hc.n_params), c);
+  SV_CUDA(grow(c->grad, c->grad_cap, (size_t)hc.n_params), c);
+  if (n_ops)
+    SV_CUDA(cudaMemcpyAsync(c->ops, hc.ops.data(), n_ops * sizeof(DOp), cudaMemcpyHostToDevice,
+                            c->stream), c);
+  return SV_OK;
+}
+
+static sv_status forward(sv_ctx* c, const HostCircuit& hc, const double* theta_dev) {
+  const int n_ops = (int)hc.ops.size();
+  SV_CUDA(launch_prep_coefs(c->ops, n_ops, theta_dev, c->coef, c->stream), c);
+  for (int l = 0; l < n_ops; ++l)
+    SV_CUDA(launch_apply_op(c->psi, c->n, hc.ops[l], c->coef + l, false, c->stream), c);
+  return SV_OK;
+}
+
+// psi = |ref>, forward, lambda = H psi, adjoint sweep; energy -> energy_dev[0], gradient ->
+// grad_dev.  Everything stream-ordered on c->stream.
+static sv_status adjoint_core(sv_ctx* c, const HostCircuit& hc, const sv_ham* H,
+                              const double* theta_dev, double* energy_dev, double* grad_dev) {
+  SV_CUDA(launch_init_basis(c->psi, c->n, c->ref, c->stream), c);
+  sv_status st = forward(c, hc, theta_dev);
+  if (st != SV_OK) return st;
+  SV_CUDA(launch_hpsi(c->psi, c->lam, c->n, H->groups, H->n_groups, H->tables, c->epart,
+                      c->stream), c);
+  SV_CUDA(launch_sum(c->epart, kRedBlocks, energy_dev, c->stream), c);
+  const int n_ops = (int)hc.ops.size();
+  for (int l = n_ops - 1; l >= 0; --l) {
+    const DOp& op = hc.ops[l];
+    double* part = op.param >= 0 ? c->gpart + (size_t)l * kRedBlocks : nullptr;
+    SV_CUDA(launch_adjoint_op(c->psi, c->lam, c->n, op, c->coef + l, part, c->stream), c);
+  }
+  SV_CUDA(launch_reduce_grads(c->ops, n_ops, c->gpart, hc.n_params, c->contrib, grad_dev,
+                              c->stream), c);
+  return SV_OK;
+}
+
+sv_status sv_apply_circuit(sv_ctx* c, const sv_circuit* circ, const double* theta) {
+  clear_error();
+  if (!c) { set_error("NULL handle"); return SV_EINVAL; }
+  SV_CHECK_STICKY(c);
+  HostCircuit hc;
+  sv_status st = lower_circuit(circ, c->n, hc);
+  if (st != SV_OK) return st;
+  if (hc.n_params > 0 && !theta) { set_error("theta is NULL"); return SV_EINVAL; }
+  if ((st = stage_circuit(c, hc)) != SV_OK) return st;
+  if (hc.n_params)
+    SV_CUDA(cudaMemcpyAsync(c->theta, theta, hc.n_params * sizeof(double),
+                            cudaMemcpyHostToDevice, c->stream), c);
+  return forward(c, hc, c->theta);
+}
+
+sv_status sv_expval_paulisum(sv_ctx* c, const sv_ham* H, double* energy_out) {
+  clear_error();
+  if (!c || !H || !energy_out) { set_error("NULL argument"); return SV_EINVAL; }
+  SV_CHECK_STICKY(c);
+  if (H->n != c->n) { set_error("Hamiltonian has %d qubits, context %d", H->n, c->n); return SV_EINVAL; }
+  SV_CUDA(launch_hpsi(c->psi, nullptr, c->n, H->groups, H->n_groups, H->tables, c->epart,
+                      c->stream), c);
+  SV_CUDA(launch_sum(c->epart, kRedBlocks, c->scal, c->stream), c);
+  SV_CUDA(cudaMemcpyAsync(energy_out, c->scal, sizeof(double), cudaMemcpyDeviceToHost,
+                          c->stream), c);
+  SV_CUDA(cudaStreamSynchronize(c->stream), c);
+  return SV_OK;
+}
+
+sv_status sv_adjoint_grad_dev(sv_ctx* c, const sv_circuit* circ, const double* theta_dev,
+                              const sv_ham* H, double* energy_dev, double* grad_dev) {
+  clear_error();
+  if (!c || !H || !energy_dev) { set_error("NULL argument"); return SV_EINVAL; }
+  SV_CHECK_STICKY(c);
+  if (H->n != c->n) { set_error("Hamiltonian has %d qubits, context %d", H->n, c->n); return SV_EINVAL; }
+  HostCircuit hc;
+  sv_status st = lower_circuit(circ, c->n, hc);
+  if (st != SV_OK) return st;
+  if (hc.n_params > 0 && (!theta_dev || !grad_dev)) { set_error("theta/grad is NULL"); return SV_EINVAL; }
+  if ((st = stage_circuit(c, hc)) != SV_OK) return st;
+  return adjoint_core(c, hc, H, theta_dev, energy_dev, grad_dev);
+}
+
+sv_status sv_adjoint_grad(sv_ctx* c, const sv_circuit* circ, const double* theta,
+                          const sv_ham* H, double* energy_out, double* grad_out) {
+  clear_error();
+  if (!c || !H || !energy_out) { set_error("NULL argument"); return SV_EINVAL; }
+  SV_CHECK_STICKY(c);
+  if (H->n != c->n) { set_error("Hamiltonian has %d qubits, context %d", H->n, c->n); return SV_EINVAL; }
+  HostCircuit hc;
+  sv_status st = lower_circuit(circ, c->n, hc);
+  if (st != SV_OK) return st;
+  if (hc.n_params > 0 && (!theta || !grad_out)) { set_error("theta/grad is NULL"); return SV_EINVAL; }
+  if ((st = stage_circuit(c, hc)) != SV_OK) return st;
+  if (hc.n_params)
+    SV_CUDA(cudaMemcpyAsync(c->theta, theta, hc.n_params * sizeof(double),
+                            cudaMemcpyHostToDevice, c->stream), c);
+  if ((st = adjoint_core(c, hc, H, c->theta, c->scal, c->grad)) != SV_OK) return st;
+  SV_CUDA(cudaMemcpyAsync(energy_out, c->scal, sizeof(double), cudaMemcpyDeviceToHost,
+                          c->stream), c);
+  if (hc.n_params)
+    SV_CUDA(cudaMemcpyAsync(grad_out, c->grad, hc.n_params * sizeof(double),
+                            cudaMemcpyDeviceToHost, c->stream), c);
+  SV_CUDA(cudaStreamSynchronize(c->stream), c);
+  return SV_OK;
+}
+
+sv_status vqe_step(sv_ctx* c, const sv_circuit* circ, const sv_ham* H, double* theta_inout,
+                   double lr, int32_t n_steps, double* energy_out) {
+  clear_error();
+  if (!c || !H) { set_error("NULL argument"); return SV_EINVAL; }
+  SV_CHECK_STICKY(c);
+  if (n_steps < 0) { set_error("n_steps %d < 0", n_steps); return SV_EINVAL; }
+  if (H->n != c->n) { set_error("Hamiltonian has %d qubits, context %d", H->n, c->n); return SV_EINVAL; }
+  HostCircuit hc;
+  sv_status st = lower_circuit(circ, c->n, hc);
+  if (st != SV_OK) return st;
+  if (hc.n_params > 0 && !theta_inout) { set_error("theta is NULL"); return SV_EINVAL; }
+  if ((st = stage_circuit(c, hc)) != SV_OK) return st;
+  SV_CUDA(grow(c->etraj, c->etraj_cap, (size_t)std::max(1, n_steps)), c);
+  if (hc.n_params)
+    SV_CUDA(cudaMemcpyAsync(c->theta, theta_inout, hc.n_params * sizeof(double),
+                            cudaMemcpyHostToDevice, c->stream), c);
+  for (int t = 0; t < n_steps; ++t) {
+    if ((st = adjoint_core(c, hc, H, c->theta, c->scal, c->grad)) != SV_OK) return st;
+    SV_CUDA(launch_gd_update(c->theta, c->grad, hc.n_params, lr, c->scal, c->etraj + t,
+                             c->stream), c);
+  }
+  if (hc.n_params)
+    SV_CUDA(cudaMemcpyAsync(theta_inout, c->theta, hc.n_params * sizeof(double),
+                            cudaMemcpyDeviceToHost, c->stream), c);
+  if (energy_out && n_steps > 0)
+    SV_CUDA(cudaMemcpyAsync(energy_out, c->etraj, n_steps * sizeof(double),
+                            cudaMemcpyDeviceToHost, c->stream), c);
+  SV_CUDA(cudaStreamSynchronize(c->stream), c);
+  return SV_OK;
+}
+
+sv_status sv_get_state(sv_ctx* c, void* host_out) {
+  clear_error();
+  if (!c || !host_out) { set_error("NULL argument"); return SV_EINVAL; }
+  SV_CHECK_STICKY(c);
+  SV_CUDA(cudaMemcpyAsync(host_out, c->psi, sv_state_bytes(c->n), cudaMemcpyDeviceToHost,
+                          c->stream), c);
+  SV_CUDA(cudaStreamSynchronize(c->stream), c);
+  return SV_OK;
+}
+
+sv_status sv_set_state(sv_ctx* c, const void* host_in) {
+  clear_error();
+  if (!c || !host_in) { set_error("NULL argument"); return SV_EINVAL; }
+  SV_CHECK_STICKY(c);
+  SV_CUDA(cudaMemcpyAsync(c->psi, host_in, sv_state_bytes(c->n), cudaMemcpyHostToDevice,
+                          c->stream), c);
+  SV_CUDA(cudaStreamSynchronize(c->stream), c);
+  return SV_OK;
+}
+
+sv_status sv_state_device_ptr(sv_ctx* c, void** psi_dev) {
+  if (!c || !psi_dev) { set_error("NULL argument"); return SV_EINVAL; }
+  *psi_dev = c->psi;
+  return SV_OK;
+}
+
+// ------------------------------------------------------------------------------ batches
+static constexpr int kTableBitsBatch = SV_BATCH_MAX_QUBITS;  // full diagonal tables allowed
+
+sv_status sv_batch_free(sv_batch* b) {
+  if (!b) return SV_OK;
+  cudaSetDevice(b->device);
+  if (b->stream) cudaStreamSynchronize(b->stream);
+  if (b->exec) cudaGraphExecDestroy(b->exec);
+  cudaFree(b->inst);
+  cudaFree(b->order);
+  cudaFree(b->ops);
+  cudaFree(b->groups);
+  cudaFree(b->tables);
+  cudaFree(b->coef);
+  cudaFree(b->contrib);
+  cudaFree(b->counter);
+  cudaFree(b->theta);
+  cudaFree(b->energy);
+  cudaFree(b->grad);
+  if (b->own_stream && b->stream) cudaStreamDestroy(b->stream);
+  cudaGetLastError();
+  delete b;
+  return SV_OK;
+}
+
+sv_status sv_batch_create(const sv_instance* inst, int32_t n, void* stream, sv_batch** out) {
+  clear_error();
+  if (!out || (n > 0 && !inst) || n < 1) { set_error("bad arguments (n = %d)", n); return SV_EINVAL; }
+  *out = nullptr;
+  std::vector<BInst> bi(n);
+  std::vector<DOp> ops;
+  std::vector<DGroup> groups;
+  std::vector<double2> tables;
+  std::vector<double> cost(n);
+  int nmax = 1;
+  int64_t theta_off = 0;
+  for (int i = 0; i < n; ++i) {
+    const sv_instance& I = inst[i];
+    if (I.circuit.n_qubits < 1 || I.circuit.n_qubits > SV_BATCH_MAX_QUBITS) {
+      set_error("instance %d: n_qubits %d outside [1, %d]", i, I.circuit.n_qubits,
+                SV_BATCH_MAX_QUBITS);
+      return SV_EINVAL;
+    }
+    HostCircuit hc;
+    sv_status st = lower_circuit(&I.circuit, I.circuit.n_qubits, hc);
+    if (st != SV_OK) return st;
+    HostHam hh;
+    if ((st = lower_ham(&I.ham, I.circuit.n_qubits, kTableBitsBatch, hh)) != SV_OK) return st;
+    if (I.ref >= (1ull << hc.n)) { set_error("instance %d: reference index out of range", i); return SV_EINVAL; }
+    BInst& B = bi[i];
+    B.n = hc.n;
+    B.n_ops = (int)hc.ops.size();
+    B.n_groups = (int)hh.groups.size();
+    B.n_params = hc.n_params;
+    B.ref = I.ref;
+    B.op_off = (int64_t)ops.size();
+    B.grp_off = (int64_t)groups.size();
+    B.theta_off = theta_off;
+    B.pad = 0;
+    theta_off += hc.n_params;
+    const int64_t toff0 = (int64_t)tables.size();
+    for (DGroup g : hh.groups) {
+      g.toff += toff0;
+      groups.push_back(g);
+    }
+    tables.insert(tables.end(), hh.tables.begin(), hh.tables.end());
+    ops.insert(ops.end(), hc.ops.begin(), hc.ops.end());
+    nmax = std::max(nmax, hc.n);
+    cost[i] = (double)(1u << hc.n) * (3.0 * B.n_ops + 1.0 * B.n_groups + 8.0);
+  }
+  sv_batch* b = new (std::nothrow) sv_batch();
+  if (!b) { set_error("host allocation failed"); return SV_ENOMEM; }
+  b->n_inst = n;
+  b->nmax = nmax;
+  b->total_params = theta_off;
+  b->total_ops = (int64_t)ops.size();
+  cudaGetDevice(&b->device);
+  if (stream) {
+    b->stream = (cudaStream_t)stream;
+  } else {
+    cudaError_t e = cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking);
+    if (e != cudaSuccess) { set_error("cudaStreamCreate: %s", cudaGetErrorString(e)); delete b; return SV_ECUDA; }
+    b->own_stream = true;
+  }
+  std::vector<int32_t> order(n);
+  std::iota(order.begin(), order.end(), 0);
+  std::stable_sort(order.begin(), order.end(), [&](int a, int c) { return cost[a] > cost[c]; });
+  auto alloc = [&](void** p, size_t bytes) {
+    return cudaMalloc(p, std::max<size_t>(bytes, 16)) == cudaSuccess;
+  };
+  const size_t P = (size_t)std::max<int64_t>(theta_off, 1);
+  if (!alloc((void**)&b->inst, n * sizeof(BInst)) || !alloc((void**)&b->order, n * sizeof(int32_t)) ||
+      !alloc((void**)&b->ops, ops.size() * sizeof(DOp)) ||
+      !alloc((void**)&b->groups, groups.size() * sizeof(DGroup)) ||
+      !alloc((void**)&b->tables, tables.size() * sizeof(double2)) ||
+      !alloc((void**)&b->coef, ops.size() * sizeof(Rot)) ||
+      !alloc((void**)&b->contrib, ops.size() * sizeof(double)) ||
+      !alloc((void**)&b->counter, sizeof(int)) || !alloc((void**)&b->theta, P * sizeof(double)) ||
+      !alloc((void**)&b->energy, n * sizeof(double)) || !alloc((void**)&b->grad, P * sizeof(double))) {
+    cudaGetLastError();
+    set_error("device allocation for a batch of %d instances failed", n);
+    sv_batch_free(b);
+    return SV_ENOMEM;
+  }
+  auto up = [&](void* d, const void* h, size_t bytes) {
+    return bytes == 0 ? cudaSuccess
+                      : cudaMemcpyAsync(d, h, bytes, cudaMemcpyHostToDevice, b->stream);
+  };
+  cudaError_t e = cudaSuccess;
+  if ((e = up(b->inst, bi.data(), n * sizeof(BInst))) != cudaSuccess ||
+      (e = up(b->order, order.data(), n * sizeof(int32_t))) != cudaSuccess ||
+      (e = up(b->ops, ops.data(), ops.size() * sizeof(DOp))) != cudaSuccess ||
+      (e = up(b->groups, groups.data(), groups.size() * sizeof(DGroup))) != cudaSuccess ||
+      (e = up(b->tables, tables.data(), tables.size() * sizeof(double2))) != cudaSuccess ||
+      (e = cudaStreamSynchronize(b->stream)) != cudaSuccess ||
+      (e = batch_prepare(nmax, &b->grid)) != cudaSuccess) {
+    set_error("batch upload failed: %s", cudaGetErrorString(e));
+    sv_batch_free(b);
+    return SV_ECUDA;
+  }
+  b->grid = std::min(b->grid, n);
+  b->smem = batch_smem_bytes(nmax);
+  *out = b;
+  return SV_OK;
+}
+
+sv_status sv_batch_info(const sv_batch* b, int32_t* n_inst, int64_t* n_params) {
+  if (!b) { set_error("NULL handle"); return SV_EINVAL; }
+  if (n_inst) *n_inst = b->n_inst;
+  if (n_params) *n_params = b->total_params;
+  return SV_OK;
+}
+
+static BatchArgs batch_args(sv_batch* b, double* theta, double* energy, double* grad,
+                            int n_steps, double lr, double* etraj) {
+  BatchArgs a;
+  a.inst = b->inst;
+  a.order = b->order;
+  a.n_inst = b->n_inst;
+  a.ops = b->ops;
+  a.groups = b->groups;
+  a.tables = b->tables;
+  a.theta = theta;
+  a.energy = energy;
+  a.grad = grad;
+  a.coef = b->coef;
+  a.contrib = b->contrib;
+  a.counter = b->counter;
+  a.n_steps = n_steps;
+  a.lr = lr;
+  a.lr_inst = nullptr;
+  a.etraj = etraj;
+  return a;
+}
+
+sv_status sv_batch_run_dev(sv_batch* b, const double* theta_dev, double* energy_dev,
+                           double* grad_dev) {
+  clear_error();
+  if (!b || !theta_dev || !energy_dev || !grad_dev) { set_error("NULL argument"); return SV_EINVAL; }
+  SV_CHECK_STICKY(b);
+  const void* key[3] = {theta_dev, energy_dev, grad_dev};
+  if (!b->exec || std::memcmp(key, b->key, sizeof key) != 0) {
+    if (b->exec) { cudaGraphExecDestroy(b->exec); b->exec = nullptr; }
+    cudaGraph_t g = nullptr;
+    SV_CUDA(cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal), b);
+    cudaError_t e1 = cudaMemsetAsync(b->counter, 0, sizeof(int), b->stream);
+    cudaError_t e2 = launch_batch(batch_args(b, const_cast<double*>(theta_dev), energy_dev,
+                                             grad_dev, 0, 0.0, nullptr),
+                                  b->grid, b->smem, b->stream);
+    cudaError_t e3 = cudaStreamEndCapture(b->stream, &g);
+    SV_CUDA(e1, b);
+    SV_CUDA(e2, b);
+    SV_CUDA(e3, b);
+    cudaError_t e = cudaGraphInstantiate(&b->exec, g, 0);
+    cudaGraphDestroy(g);
+    SV_CUDA(e, b);
+    std::memcpy(b->key, key, sizeof key);
+  }
+  SV_CUDA(cudaGraphLaunch(b->exec, b->stream), b);
+  return SV_OK;
+}
+
+sv_status sv_batch_run(sv_batch* b, const double* theta, double* energy, double* grad) {
+  clear_error();
+  if (!b || (b->total_params > 0 && (!theta || !grad)) || !energy) { set_error("NULL argument"); return SV_EINVAL; }
+  SV_CHECK_STICKY(b);
+  if (b->total_params)
+    SV_CUDA(cudaMemcpyAsync(b->theta, theta, b->total_params * sizeof(double),
+                            cudaMemcpyHostToDevice, b->stream), b);
+  sv_status st = sv_batch_run_dev(b, b->theta, b->energy, b->grad);
+  if (st != SV_OK) return st;
+  SV_CUDA(cudaMemcpyAsync(energy, b->energy, b->n_inst * sizeof(double), cudaMemcpyDeviceToHost,
+                          b->stream), b);
+  if (b->total_params)
+    SV_CUDA(cudaMemcpyAsync(grad, b->grad, b->total_params * sizeof(double),
+                            cudaMemcpyDeviceToHost, b->stream), b);
+  SV_CUDA(cudaStreamSynchronize(b->stream), b);
+  return SV_OK;
+}
+
+sv_status sv_batch_vqe_dev(sv_batch* b, double* theta_dev, double lr, int32_t n_steps,
+                           double* energy_traj_dev) {
+  clear_error();
+  if (!b || !theta_dev) { set_error("NULL argument"); return SV_EINVAL; }
+  if (n_steps < 1) { set_error("n_steps %d < 1", n_steps); return SV_EINVAL; }
+  SV_CHECK_STICKY(b);
+  SV_CUDA(cudaMemsetAsync(b->counter, 0, sizeof(int), b->stream), b);
+  SV_CUDA(launch_batch(batch_args(b, theta_dev, b->energy, b->grad, n_steps, lr,
+                                  energy_traj_dev), b->grid, b->smem, b->stream), b);
+  return SV_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,44 @@
+// host_compile.h -- host-side validation and lowering of circuits and Pauli sums.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/svqe.h"
+
+namespace svqe {
+
+struct DOp;
+struct DGroup;
+
+// Thread-local error message (sv_last_error).
+void set_error(const char* fmt, ...);
+void clear_error();
+const char* last_error();
+
+// A circuit lowered to device op records (see DOp).  Gates are validated: known type, wires
+// in [0, n), distinct wires, parameter index in [-1, n_params).
+struct HostCircuit {
+  int n = 0;
+  int n_params = 0;
+  std::vector<DOp> ops;
+};
+sv_status lower_circuit(const sv_circuit* c, int expect_n, HostCircuit& out);
+
+// A Pauli sum grouped by X mask.  Every group's f(k) = sum_t c_t (-i)^{popc(x&z_t)}
+// (-1)^{popc(z_t&k)} is tabulated over the kz bits of the union zu of its z masks, so that
+// (H psi)[k] = sum_g f_g(k) psi[k ^ x_g].  A group whose union would exceed kmax bits is split
+// into several groups with the same x.  The x = 0 group, if any, comes first.
+struct HostHam {
+  int n = 0;
+  int n_terms = 0;
+  double l1 = 0.0;  // sum |c_t|
+  std::vector<DGroup> groups;
+  std::vector<double2> tables;
+};
+sv_status lower_ham(const sv_paulisum* h, int expect_n, int kmax, HostHam& out);
+
+}  // namespace svqe

@@ -1,0 +1,75 @@
+// launch.h -- host-callable launchers of the single-state kernels (k_state.cu).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "svqe_types.h"
+
+namespace svqe {
+
+// Fixed grid for reductions: partial arrays hold at most kRedBlocks values per launch.
+constexpr int kRedBlocks = 1216;  // 152 SMs x 8
+constexpr int kThreads = 256;
+
+cudaError_t launch_init_basis(double2* psi, int n, uint64_t b, cudaStream_t s);
+cudaError_t launch_prep_coefs(const DOp* ops, int n_ops, const double* theta, Rot* coefs,
+                              cudaStream_t s);
+// Apply (inv = false) or un-apply one op on psi; coef points at the op's Rot.
+cudaError_t launch_apply_op(double2* psi, int n, const DOp& op, const Rot* coef, bool inv,
+                            cudaStream_t s);
+// Adjoint step for one op: if the op is parameterised, partial[b] (b < kRedBlocks) receives
+// block b's share of 2 Im<lambda|G|psi>; then psi and lambda are un-applied.
+cudaError_t launch_adjoint_op(double2* psi, double2* lam, int n, const DOp& op, const Rot* coef,
+                              double* partial, cudaStream_t s);
+// lambda = H psi (if lam != nullptr) and partial[b] = block b's share of Re<psi|H psi>.
+cudaError_t launch_hpsi(const double2* psi, double2* lam, int n, const DGroup* groups,
+                        int n_groups, const double2* tables, double* partial, cudaStream_t s);
+// out[0] = sum of partial[0..count) in a fixed order.
+cudaError_t launch_sum(const double* partial, int count, double* out, cudaStream_t s);
+// grad[p] = sum over ops l with param p (in op order) of sum_b partial[l * kRedBlocks + b].
+cudaError_t launch_reduce_grads(const DOp* ops, int n_ops, const double* partial, int n_params,
+                                double* contrib, double* grad, cudaStream_t s);
+// theta -= lr * grad (n entries); optionally records energy[0] into traj[step].
+cudaError_t launch_gd_update(double* theta, const double* grad, int n, double lr,
+                             const double* energy, double* traj, cudaStream_t s);
+
+}  // namespace svqe
+
+namespace svqe {
+
+// One instance of a compiled batch (device record).
+struct BInst {
+  int32_t n, n_ops, n_groups, n_params;
+  uint64_t ref;
+  int64_t op_off, grp_off, theta_off;
+  int64_t pad;
+};
+static_assert(sizeof(BInst) == 56, "BInst layout");
+
+struct BatchArgs {
+  const BInst* inst;
+  const int32_t* order;    // instance indices, most expensive first
+  int n_inst;
+  const DOp* ops;
+  const DGroup* groups;
+  const double2* tables;
+  double* theta;           // concatenated parameters (updated in place when n_steps > 0)
+  double* energy;          // [n_inst]
+  double* grad;            // concatenated gradients
+  Rot* coef;               // scratch, one per op
+  double* contrib;         // scratch, one per op
+  int* counter;            // work-queue head, zeroed before each launch
+  int n_steps;             // 0: one evaluation; > 0: that many gradient-descent updates
+  double lr;               // step when lr_inst == nullptr
+  const double* lr_inst;   // per-instance steps, or nullptr
+  double* etraj;           // [n_steps x n_inst] energies before each update, or nullptr
+};
+
+// Threads per CTA of the batched kernel and its dynamic shared memory for nmax qubits.
+constexpr int kBatchThreads = 256;
+size_t batch_smem_bytes(int nmax);
+cudaError_t batch_prepare(int nmax, int* grid_out);
+cudaError_t launch_batch(const BatchArgs& a, int grid, size_t smem, cudaStream_t s);
+
+}  // namespace svqe

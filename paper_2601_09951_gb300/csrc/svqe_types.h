@@ -1,0 +1,54 @@
+// svqe_types.h -- record layouts shared by host lowering and device kernels.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/svqe.h"
+
+namespace svqe {
+
+// ------------------------------------------------------------------------------ op records
+// A compiled gate.  Its amplitude "pairs" are enumerated by inserting zero bits at the
+// sorted positions sb[0..k) into a counter p in [0, 2^(n-k)), OR-ing `lo_or`, and pairing the
+// result i with j = i ^ flip (flip = 0: a single amplitude, e.g. CZ).
+struct DOp {
+  int32_t type;    // SV_GATE_*
+  int32_t param;   // theta index or -1
+  int32_t k;       // number of inserted zero bits
+  int32_t bit0;    // basis-index bit of the first wire (1-qubit gates)
+  uint8_t sb[4];   // sorted bit positions of the wires
+  int32_t pad;
+  uint64_t lo_or;  // bits set in the first amplitude of each pair
+  uint64_t flip;   // XOR mask from the first to the second amplitude
+  double fixed;    // angle when param < 0
+};
+static_assert(sizeof(DOp) == 48, "DOp layout");
+
+// Lifting form of the rotation R(phi) = [[c, -s], [s, c]] (phi = theta/2):
+// R(phi) = L(a) S(b) L(a) R(k pi/2), a = -tan(r/2), b = sin(r), r = phi - k pi/2 in
+// [-pi/4, pi/4].
+struct Rot {
+  double a, b;
+  int32_t k;
+  int32_t pad;
+};
+static_assert(sizeof(Rot) == 24, "Rot layout");
+
+// An X-mask group of Pauli terms: f(i) = table[pext(i, zu)], cls says whether the table is
+// real (0), purely imaginary (1) or complex (2).
+struct DGroup {
+  uint64_t x;
+  uint64_t zu;
+  int32_t kz;
+  int32_t cls;
+  int64_t toff;  // offset of the table (double2 entries)
+};
+static_assert(sizeof(DGroup) == 32, "DGroup layout");
+
+__host__ __device__ __forceinline__ bool is_param_type(int t) {
+  return t == SV_GATE_RX || t == SV_GATE_RY || t == SV_GATE_RZ || t == SV_GATE_SINGLE_EXC ||
+         t == SV_GATE_DOUBLE_EXC;
+}
+
+}  // namespace svqe

@@ -1,0 +1,337 @@
+"""ctypes binding of libsvqe.so (the C ABI in include/svqe.h).
+
+Argument marshalling only: every step of the hot path runs in the library's CUDA kernels.
+There is no CPU fallback; if the library is missing or fails to load, every call raises.
+Build it with ``paper_2601_09951_gb300.build.build()`` (or ``__graft_entry__.build()``).
+"""
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+
+SV_OK, SV_EINVAL, SV_ENOMEM, SV_ECUDA, SV_ETIMEOUT, SV_EUNSUPPORTED, SV_EBUSY = range(7)
+BATCH_MAX_QUBITS = 12
+
+GATE_DTYPE = np.dtype([("type", "<i4"), ("wires", "<i4", (4,)), ("param", "<i4"),
+                       ("fixed_angle", "<f8")], align=True)
+assert GATE_DTYPE.itemsize == 32
+
+
+class SvError(RuntimeError):
+    def __init__(self, status, message):
+        super().__init__(f"{_STATUS.get(status, status)}: {message}")
+        self.status = status
+
+
+_STATUS = {0: "SV_OK", 1: "SV_EINVAL", 2: "SV_ENOMEM", 3: "SV_ECUDA", 4: "SV_ETIMEOUT",
+           5: "SV_EUNSUPPORTED", 6: "SV_EBUSY"}
+
+
+class _Circuit(ctypes.Structure):
+    _fields_ = [("n_qubits", ctypes.c_int32), ("n_gates", ctypes.c_int32),
+                ("n_params", ctypes.c_int32), ("gates", ctypes.c_void_p)]
+
+
+class _PauliSum(ctypes.Structure):
+    _fields_ = [("n_qubits", ctypes.c_int32), ("n_terms", ctypes.c_int32),
+                ("x_mask", ctypes.c_void_p), ("z_mask", ctypes.c_void_p),
+                ("coeff", ctypes.c_void_p)]
+
+
+class _Instance(ctypes.Structure):
+    _fields_ = [("circuit", _Circuit), ("ham", _PauliSum), ("ref", ctypes.c_uint64)]
+
+
+_lib = None
+
+
+def lib_path():
+    return _build.LIB
+
+
+def lib():
+    """The loaded library.  Raises if it has not been built: the product path has no
+    fallback."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = _build.LIB
+    if not os.path.exists(path):
+        raise RuntimeError(f"{path} is missing: build the CUDA library first "
+                           "(paper_2601_09951_gb300.build.build())")
+    L = ctypes.CDLL(path)
+    P, i32, i64, u64, dbl = (ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_uint64,
+                             ctypes.c_double)
+    sigs = {
+        "sv_status_str": ([i32], ctypes.c_char_p),
+        "sv_last_error": ([], ctypes.c_char_p),
+        "sv_abi_version": ([], i32),
+        "sv_state_bytes": ([i32], u64),
+        "sv_ctx_device_bytes": ([i32], u64),
+        "sv_create": ([P, i32, P], i32),
+        "sv_destroy": ([P], i32),
+        "sv_ham_upload": ([P, P, P], i32),
+        "sv_ham_free": ([P], i32),
+        "sv_ham_info": ([P, P, P], i32),
+        "sv_ham_lower": ([P, i32, P, P, P, P, P, P, P], i32),
+        "sv_init_reference": ([P, u64], i32),
+        "sv_apply_circuit": ([P, P, P], i32),
+        "sv_expval_paulisum": ([P, P, P], i32),
+        "sv_adjoint_grad": ([P, P, P, P, P, P], i32),
+        "sv_adjoint_grad_dev": ([P, P, P, P, P, P], i32),
+        "vqe_step": ([P, P, P, P, dbl, i32, P], i32),
+        "sv_get_state": ([P, P], i32),
+        "sv_set_state": ([P, P], i32),
+        "sv_state_device_ptr": ([P, P], i32),
+        "sv_batch_create": ([P, i32, P, P], i32),
+        "sv_batch_free": ([P], i32),
+        "sv_batch_info": ([P, P, P], i32),
+        "sv_batch_run": ([P, P, P, P], i32),
+        "sv_batch_run_dev": ([P, P, P, P], i32),
+        "sv_batch_vqe_dev": ([P, P, dbl, i32, P], i32),
+    }
+    for name, (args, res) in sigs.items():
+        fn = getattr(L, name)
+        fn.argtypes = args
+        fn.restype = res
+    _lib = L
+    return L
+
+
+def _check(status):
+    if status != SV_OK:
+        msg = lib().sv_last_error()
+        raise SvError(status, msg.decode() if msg else "")
+
+
+def _ptr(a):
+    return None if a is None else a.ctypes.data_as(ctypes.c_void_p)
+
+
+def state_bytes(n):
+    return int(lib().sv_state_bytes(int(n)))
+
+
+def ctx_device_bytes(n):
+    return int(lib().sv_ctx_device_bytes(int(n)))
+
+
+class Circuit:
+    """Gate records of a circuit dict (see workloads) in the ABI layout."""
+
+    def __init__(self, circuit):
+        c = circuit
+        G = len(c["types"])
+        self.gates = np.zeros(G, dtype=GATE_DTYPE)
+        self.gates["type"] = np.asarray(c["types"], dtype=np.int32)
+        self.gates["wires"] = np.asarray(c["wires"], dtype=np.int32).reshape(G, 4)
+        self.gates["param"] = np.asarray(c["params"], dtype=np.int32)
+        self.gates["fixed_angle"] = np.asarray(c["fixed"], dtype=np.float64)
+        self.n = int(c["n"])
+        self.n_params = int(c["n_params"])
+        self.struct = _Circuit(self.n, G, self.n_params,
+                               self.gates.ctypes.data if G else None)
+
+    def ref(self):
+        return ctypes.byref(self.struct)
+
+
+class PauliSum:
+    def __init__(self, ham, n):
+        self.x = np.ascontiguousarray(ham["x"], dtype=np.uint64)
+        self.z = np.ascontiguousarray(ham["z"], dtype=np.uint64)
+        self.c = np.ascontiguousarray(ham["coeff"], dtype=np.float64)
+        self.n = int(n)
+        self.struct = _PauliSum(self.n, len(self.c), self.x.ctypes.data, self.z.ctypes.data,
+                                self.c.ctypes.data)
+
+    def ref(self):
+        return ctypes.byref(self.struct)
+
+
+def ham_lower(ham, n, kmax):
+    """Host-only view of the X-mask grouping: (x, zu, cls, toff, table[complex])."""
+    ps = PauliSum(ham, n)
+    ng, nt = ctypes.c_int32(0), ctypes.c_int64(0)
+    _check(lib().sv_ham_lower(ps.ref(), int(kmax), ctypes.byref(ng), ctypes.byref(nt),
+                              None, None, None, None, None))
+    x = np.zeros(ng.value, np.uint64)
+    zu = np.zeros(ng.value, np.uint64)
+    cls = np.zeros(ng.value, np.int32)
+    toff = np.zeros(ng.value, np.int64)
+    table = np.zeros(max(nt.value, 1), np.complex128)
+    _check(lib().sv_ham_lower(ps.ref(), int(kmax), ctypes.byref(ng), ctypes.byref(nt),
+                              _ptr(x), _ptr(zu), _ptr(cls), _ptr(toff), _ptr(table)))
+    return x, zu, cls, toff, table[:nt.value]
+
+
+class Ham:
+    """A device-resident grouped Pauli sum (sv_ham)."""
+
+    def __init__(self, ctx, ham):
+        self._h = ctypes.c_void_p()
+        ps = PauliSum(ham, ctx.n)
+        _check(lib().sv_ham_upload(ctx.handle, ps.ref(), ctypes.byref(self._h)))
+        self.n = ctx.n
+
+    @property
+    def handle(self):
+        return self._h
+
+    def info(self):
+        g, b = ctypes.c_int32(), ctypes.c_uint64()
+        _check(lib().sv_ham_info(self._h, ctypes.byref(g), ctypes.byref(b)))
+        return g.value, b.value
+
+    def close(self):
+        if self._h:
+            lib().sv_ham_free(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Context:
+    """One n-qubit state (sv_ctx): psi and lambda buffers on the device plus a stream."""
+
+    def __init__(self, n, stream=None):
+        self._c = ctypes.c_void_p()
+        self.n = int(n)
+        _check(lib().sv_create(ctypes.byref(self._c), self.n,
+                               ctypes.c_void_p(stream) if stream else None))
+
+    @property
+    def handle(self):
+        return self._c
+
+    def init_reference(self, b):
+        _check(lib().sv_init_reference(self._c, int(b)))
+
+    def apply_circuit(self, circuit, theta):
+        C = circuit if isinstance(circuit, Circuit) else Circuit(circuit)
+        th = np.ascontiguousarray(theta, dtype=np.float64)
+        _check(lib().sv_apply_circuit(self._c, C.ref(), _ptr(th) if th.size else None))
+
+    def expval(self, ham):
+        e = ctypes.c_double()
+        _check(lib().sv_expval_paulisum(self._c, ham.handle, ctypes.byref(e)))
+        return e.value
+
+    def adjoint_grad(self, circuit, theta, ham):
+        C = circuit if isinstance(circuit, Circuit) else Circuit(circuit)
+        th = np.ascontiguousarray(theta, dtype=np.float64)
+        g = np.zeros(max(C.n_params, 1), dtype=np.float64)
+        e = ctypes.c_double()
+        _check(lib().sv_adjoint_grad(self._c, C.ref(), _ptr(th) if th.size else None,
+                                     ham.handle, ctypes.byref(e), _ptr(g)))
+        return e.value, g[:C.n_params]
+
+    def adjoint_grad_dev(self, circuit, theta_ptr, ham, energy_ptr, grad_ptr):
+        C = circuit if isinstance(circuit, Circuit) else Circuit(circuit)
+        _check(lib().sv_adjoint_grad_dev(self._c, C.ref(), ctypes.c_void_p(theta_ptr),
+                                         ham.handle, ctypes.c_void_p(energy_ptr),
+                                         ctypes.c_void_p(grad_ptr)))
+
+    def vqe_step(self, circuit, ham, theta, lr, n_steps):
+        C = circuit if isinstance(circuit, Circuit) else Circuit(circuit)
+        th = np.array(theta, dtype=np.float64, copy=True)
+        es = np.zeros(max(n_steps, 1), dtype=np.float64)
+        _check(lib().vqe_step(self._c, C.ref(), ham.handle, _ptr(th) if th.size else None,
+                              float(lr), int(n_steps), _ptr(es)))
+        return th, es[:n_steps]
+
+    def get_state(self):
+        out = np.empty(1 << self.n, dtype=np.complex128)
+        _check(lib().sv_get_state(self._c, _ptr(out)))
+        return out
+
+    def set_state(self, psi):
+        a = np.ascontiguousarray(psi, dtype=np.complex128)
+        if a.size != 1 << self.n:
+            raise ValueError("state has the wrong size")
+        _check(lib().sv_set_state(self._c, _ptr(a)))
+
+    def state_ptr(self):
+        p = ctypes.c_void_p()
+        _check(lib().sv_state_device_ptr(self._c, ctypes.byref(p)))
+        return p.value
+
+    def close(self):
+        if self._c:
+            lib().sv_destroy(self._c)
+            self._c = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Batch:
+    """Many small instances (n <= 12) compiled for the persistent batched kernel."""
+
+    def __init__(self, instances, stream=None):
+        self._b = ctypes.c_void_p()
+        self._keep = []
+        arr = (_Instance * len(instances))()
+        offs = [0]
+        for i, inst in enumerate(instances):
+            C = Circuit(inst["circuit"])
+            H = PauliSum(inst["ham"], C.n)
+            self._keep += [C, H]
+            arr[i].circuit = C.struct
+            arr[i].ham = H.struct
+            arr[i].ref = int(inst["ref"])
+            offs.append(offs[-1] + C.n_params)
+        self.offsets = np.array(offs, dtype=np.int64)
+        _check(lib().sv_batch_create(arr, len(instances),
+                                     ctypes.c_void_p(stream) if stream else None,
+                                     ctypes.byref(self._b)))
+        self._keep = None
+        ni, npar = ctypes.c_int32(), ctypes.c_int64()
+        _check(lib().sv_batch_info(self._b, ctypes.byref(ni), ctypes.byref(npar)))
+        self.n_instances, self.n_params = ni.value, npar.value
+
+    def theta_of(self, instances):
+        return np.concatenate([np.asarray(i["theta"], np.float64) for i in instances]) \
+            if self.n_params else np.zeros(0)
+
+    def run(self, theta, energy_out=None, grad_out=None):
+        """Host buffers in and out (copies included).  Returns (energy[n], grad[P])."""
+        th = np.ascontiguousarray(theta, dtype=np.float64)
+        e = energy_out if energy_out is not None else np.empty(self.n_instances, np.float64)
+        g = grad_out if grad_out is not None else np.empty(max(self.n_params, 1), np.float64)
+        _check(lib().sv_batch_run(self._b, _ptr(th), _ptr(e), _ptr(g)))
+        return e, g[:self.n_params]
+
+    def run_ptr(self, theta_ptr, energy_ptr, grad_ptr, energy_host_ptr=None):
+        """Host pointers (e.g. pinned tensors): the same call as run(), without numpy."""
+        _check(lib().sv_batch_run(self._b, ctypes.c_void_p(theta_ptr),
+                                  ctypes.c_void_p(energy_ptr), ctypes.c_void_p(grad_ptr)))
+
+    def run_dev(self, theta_ptr, energy_ptr, grad_ptr):
+        _check(lib().sv_batch_run_dev(self._b, ctypes.c_void_p(theta_ptr),
+                                      ctypes.c_void_p(energy_ptr), ctypes.c_void_p(grad_ptr)))
+
+    def vqe_dev(self, theta_ptr, lr, n_steps, etraj_ptr=None):
+        _check(lib().sv_batch_vqe_dev(self._b, ctypes.c_void_p(theta_ptr), float(lr),
+                                      int(n_steps),
+                                      ctypes.c_void_p(etraj_ptr) if etraj_ptr else None))
+
+    def close(self):
+        if self._b:
+            lib().sv_batch_free(self._b)
+            self._b = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,116 @@
+"""CPU-only checks of the C ABI: the library loads, exports every declared symbol, and its
+host-side logic (sizes, validation, X-mask grouping with Walsh-Hadamard tables) is right.
+No compute call needs a GPU here."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+from paper_2601_09951_gb300 import svqe
+from paper_2601_09951_gb300 import workloads as W
+from tests import dense_pins as D
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    from paper_2601_09951_gb300 import build
+    build.build()
+
+
+def _declared():
+    names = set()
+    for f in os.listdir(os.path.join(ROOT, "include")):
+        if f.endswith(".h"):
+            src = open(os.path.join(ROOT, "include", f)).read()
+            src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+            for m in re.finditer(r"^\s*[A-Za-z_][\w\s\*]*?\b((?:sv|vqe)_\w+)\s*\(", src, re.M):
+                names.add(m.group(1))
+    return names
+
+
+def test_every_declared_symbol_is_exported():
+    names = _declared()
+    assert {"sv_init_reference", "sv_apply_circuit", "sv_expval_paulisum", "sv_adjoint_grad",
+            "vqe_step", "sv_batch_run"} <= names
+    L = ctypes.CDLL(svqe.lib_path())
+    missing = [n for n in sorted(names) if not hasattr(L, n)]
+    assert not missing, missing
+
+
+def test_state_sizes_match_table3():
+    """Fixture tests/golden/table3_state_bytes.txt: Table 3's state-vector column."""
+    rows = [l.split() for l in open(os.path.join(ROOT, "tests", "golden",
+                                                 "table3_state_bytes.txt"))
+            if l.strip() and not l.startswith("#")]
+    unit = {"B": 1, "KB": 1 << 10, "MB": 1 << 20, "GB": 1 << 30}
+    for n, val, u in rows:
+        assert svqe.state_bytes(int(n)) == int(val) * unit[u]
+    # Two state buffers for 31 qubits fit in HBM with room for a third.
+    assert svqe.ctx_device_bytes(31) < 3 * svqe.state_bytes(31)
+    assert svqe.state_bytes(-1) == 0 and svqe.ctx_device_bytes(32) == 0
+
+
+def test_status_strings_and_version():
+    L = svqe.lib()
+    assert L.sv_abi_version() == 1
+    assert L.sv_status_str(1) == b"SV_EINVAL"
+
+
+def test_bad_qubit_count_is_einval_without_touching_the_gpu():
+    for n in (0, 32, -3):
+        with pytest.raises(svqe.SvError) as e:
+            svqe.Context(n)
+        assert e.value.status == svqe.SV_EINVAL
+
+
+def _apply_lowered(n, lowered, psi):
+    x, zu, cls, toff, table = lowered
+    out = np.zeros_like(psi)
+    ks = np.arange(1 << n, dtype=np.uint64)
+    for g in range(len(x)):
+        idx = np.zeros(1 << n, dtype=np.int64)
+        m, b = int(zu[g]), 0
+        while m:
+            pos = (m & -m).bit_length() - 1
+            idx |= (((ks >> np.uint64(pos)) & np.uint64(1)).astype(np.int64)) << b
+            b += 1
+            m &= m - 1
+        out += table[toff[g] + idx] * psi[(ks ^ x[g]).astype(np.int64)]
+    return out
+
+
+@pytest.mark.parametrize("n,kmax", [(3, 3), (6, 2), (6, 6), (9, 4)])
+def test_grouped_tables_reproduce_dense_h_psi(n, kmax):
+    rng = np.random.default_rng(n * 10 + kmax)
+    ham = W.random_pauli_sum(rng, n, 120, 0.4, min(4, n), 1.0)
+    # several terms sharing one X mask with mixed Y parity (complex tables)
+    for s in ("XYZ", "YXZ", "XXZ", "YYI"):
+        f = {q: p for q, p in enumerate(s) if p != "I"}
+        x, z = W.pauli_masks(n, f)
+        ham["x"] = np.append(ham["x"], np.uint64(x))
+        ham["z"] = np.append(ham["z"], np.uint64(z))
+        ham["coeff"] = np.append(ham["coeff"], rng.normal())
+    lowered = svqe.ham_lower(ham, n, kmax)
+    widest = max(bin(int(z)).count("1") for z in ham["z"])
+    assert np.all([bin(int(z)).count("1") <= max(kmax, widest) for z in lowered[1]])
+    psi = rng.normal(size=1 << n) + 1j * rng.normal(size=1 << n)
+    want = D.ham_dense(n, ham) @ psi
+    np.testing.assert_allclose(_apply_lowered(n, lowered, psi), want, atol=1e-12)
+    # groups share no X mask with a different class than their table needs
+    for g, c in enumerate(lowered[2]):
+        t = lowered[4][lowered[3][g]: lowered[3][g] + (1 << bin(int(lowered[1][g])).count("1"))]
+        if c == 0:
+            assert np.all(t.imag == 0)
+        if c == 1:
+            assert np.all(t.real == 0)
+
+
+def test_lowering_rejects_bad_masks():
+    with pytest.raises(svqe.SvError) as e:
+        svqe.ham_lower({"x": np.array([8], np.uint64), "z": np.array([0], np.uint64),
+                        "coeff": np.array([1.0])}, 3, 3)
+    assert e.value.status == svqe.SV_EINVAL

@@ -1,0 +1,101 @@
+"""GPU parity of the persistent batched kernel (sv_batch_*) against the CPU oracle, and the
+batching identity: an instance's result is bit-identical alone and inside any batch."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2601_09951_gb300 import svqe
+from paper_2601_09951_gb300 import workloads as W
+from tests.parity import assert_energy, assert_grad
+
+pytestmark = pytest.mark.gpu
+
+
+def _check(batch, insts, energy, grad):
+    for i, inst in enumerate(insts):
+        e0, g0 = oracle.energy_grad(inst)
+        assert_energy(energy[i], e0, inst["ham"], inst["name"])
+        a, b = batch.offsets[i], batch.offsets[i + 1]
+        assert_grad(grad[a:b], g0, inst["ham"], inst["name"])
+
+
+def test_h2_sweep_batch():
+    insts = W.h2_sweep(100)
+    for k, inst in enumerate(insts):
+        inst["theta"] = np.array([0.05 * k - 2.0])
+    b = svqe.Batch(insts)
+    e, g = b.run(b.theta_of(insts))
+    _check(b, insts, e, g)
+
+
+def test_hea_batch_small_sample():
+    insts = W.hea_batch(48)
+    b = svqe.Batch(insts)
+    e, g = b.run(b.theta_of(insts))
+    _check(b, insts, e, g)
+
+
+def test_mixed_gate_batch_with_ragged_sizes():
+    insts = [W.uccsd_instance(n=n, n_elec=n // 2, n_singles=6, n_doubles=6, n_terms=60,
+                              seed=n) for n in (4, 7, 12)]
+    insts += [W.hea_instance(n, 2, 40, n, ring=True) for n in (1, 2, 3, 5, 12)]
+    insts += W.h2_sweep(5)
+    b = svqe.Batch(insts)
+    e, g = b.run(b.theta_of(insts))
+    _check(b, insts, e, g)
+
+
+def test_batching_identity_bitwise():
+    insts = W.hea_batch(40)
+    big = svqe.Batch(insts)
+    e_all, g_all = big.run(big.theta_of(insts))
+    for i in (0, 7, 23, 39):
+        one = svqe.Batch([insts[i]])
+        e1, g1 = one.run(one.theta_of([insts[i]]))
+        assert e1[0] == e_all[i]
+        a, b = big.offsets[i], big.offsets[i + 1]
+        assert np.array_equal(g1, g_all[a:b])
+    sub = [insts[j] for j in (39, 3, 17)]
+    sb = svqe.Batch(sub)
+    es, gs = sb.run(sb.theta_of(sub))
+    for k, j in enumerate((39, 3, 17)):
+        assert es[k] == e_all[j]
+
+
+def test_device_buffers_and_graph_replay():
+    torch = pytest.importorskip("torch")
+    insts = W.hea_batch(16)
+    b = svqe.Batch(insts)
+    th = torch.tensor(b.theta_of(insts), dtype=torch.float64, device="cuda")
+    e = torch.empty(len(insts), dtype=torch.float64, device="cuda")
+    g = torch.empty(b.n_params, dtype=torch.float64, device="cuda")
+    e_h, g_h = b.run(b.theta_of(insts))
+    for _ in range(3):
+        b.run_dev(th.data_ptr(), e.data_ptr(), g.data_ptr())
+    torch.cuda.synchronize()
+    assert np.array_equal(e.cpu().numpy(), e_h)
+    assert np.array_equal(g.cpu().numpy(), g_h)
+
+
+def test_on_device_gradient_descent_h2():
+    torch = pytest.importorskip("torch")
+    insts = W.h2_sweep(100)[::20]
+    b = svqe.Batch(insts)
+    lr, T = 0.4, 50
+    th = torch.zeros(len(insts), dtype=torch.float64, device="cuda")
+    traj = torch.empty(T, len(insts), dtype=torch.float64, device="cuda")
+    b.vqe_dev(th.data_ptr(), lr, T, traj.data_ptr())
+    torch.cuda.synchronize()
+    traj = traj.cpu().numpy()
+    # per-step parity: replay the trajectory one step at a time and check E_t, g_t
+    th1 = torch.zeros(len(insts), dtype=torch.float64, device="cuda")
+    for t in range(T):
+        before = th1.cpu().numpy().copy()
+        b.vqe_dev(th1.data_ptr(), lr, 1, None)
+        torch.cuda.synchronize()
+        after = th1.cpu().numpy()
+        for i, inst in enumerate(insts):
+            e0, g0 = oracle.energy_grad(inst, before[i:i + 1])
+            assert_energy(traj[t, i], e0, inst["ham"], f"{inst['name']} step {t}")
+            assert_grad((before[i:i + 1] - after[i:i + 1]) / lr, g0, inst["ham"])
+    assert np.array_equal(th.cpu().numpy(), th1.cpu().numpy())
