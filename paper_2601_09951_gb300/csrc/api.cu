@@ -69,8 +69,13 @@ struct sv_batch {
   DOp* ops = nullptr;
   DGroup* groups = nullptr;
   double2* tables = nullptr;
+  Seg* segs = nullptr;
+  int32_t* pptr = nullptr;
+  int32_t* pops = nullptr;
   Rot* coef = nullptr;
   double* contrib = nullptr;
+  double2* ckpt = nullptr;
+  int64_t ckpt_slot = 0;
   int* counter = nullptr;
   double* theta = nullptr;   // owned buffers for the host-pointer entry point
   double* energy = nullptr;
@@ -483,8 +488,12 @@ sv_status sv_batch_free(sv_batch* b) {
   cudaFree(b->ops);
   cudaFree(b->groups);
   cudaFree(b->tables);
+  cudaFree(b->segs);
+  cudaFree(b->pptr);
+  cudaFree(b->pops);
   cudaFree(b->coef);
   cudaFree(b->contrib);
+  cudaFree(b->ckpt);
   cudaFree(b->counter);
   cudaFree(b->theta);
   cudaFree(b->energy);
@@ -503,9 +512,11 @@ sv_status sv_batch_create(const sv_instance* inst, int32_t n, void* stream, sv_b
   std::vector<DOp> ops;
   std::vector<DGroup> groups;
   std::vector<double2> tables;
+  std::vector<Seg> segs;
+  std::vector<int32_t> pptr, pops;
   std::vector<double> cost(n);
   int nmax = 1;
-  int64_t theta_off = 0;
+  int64_t theta_off = 0, ckpt_slot = 1;
   for (int i = 0; i < n; ++i) {
     const sv_instance& I = inst[i];
     if (I.circuit.n_qubits < 1 || I.circuit.n_qubits > SV_BATCH_MAX_QUBITS) {
@@ -519,17 +530,33 @@ sv_status sv_batch_create(const sv_instance* inst, int32_t n, void* stream, sv_b
     HostHam hh;
     if ((st = lower_ham(&I.ham, I.circuit.n_qubits, kTableBitsBatch, hh)) != SV_OK) return st;
     if (I.ref >= (1ull << hc.n)) { set_error("instance %d: reference index out of range", i); return SV_EINVAL; }
+    std::vector<Seg> sg;
+    const int n_ckpt = segment_ops(hc.ops, 2, 3, sg);
     BInst& B = bi[i];
     B.n = hc.n;
     B.n_ops = (int)hc.ops.size();
     B.n_groups = (int)hh.groups.size();
     B.n_params = hc.n_params;
+    B.n_segs = (int)sg.size();
+    B.n_ckpt = n_ckpt;
     B.ref = I.ref;
     B.op_off = (int64_t)ops.size();
     B.grp_off = (int64_t)groups.size();
     B.theta_off = theta_off;
-    B.pad = 0;
+    B.seg_off = (int64_t)segs.size();
+    B.pp_off = (int64_t)pptr.size();
     theta_off += hc.n_params;
+    ckpt_slot = std::max<int64_t>(ckpt_slot, (int64_t)n_ckpt << hc.n);
+    segs.insert(segs.end(), sg.begin(), sg.end());
+    // parameter -> ops using it, in op order (CSR)
+    std::vector<std::vector<int32_t>> uses(hc.n_params);
+    for (int l = 0; l < (int)hc.ops.size(); ++l)
+      if (hc.ops[l].param >= 0) uses[hc.ops[l].param].push_back(l);
+    for (int p = 0; p < hc.n_params; ++p) {
+      pptr.push_back((int32_t)pops.size());
+      pops.insert(pops.end(), uses[p].begin(), uses[p].end());
+    }
+    pptr.push_back((int32_t)pops.size());
     const int64_t toff0 = (int64_t)tables.size();
     for (DGroup g : hh.groups) {
       g.toff += toff0;
@@ -565,6 +592,9 @@ sv_status sv_batch_create(const sv_instance* inst, int32_t n, void* stream, sv_b
       !alloc((void**)&b->ops, ops.size() * sizeof(DOp)) ||
       !alloc((void**)&b->groups, groups.size() * sizeof(DGroup)) ||
       !alloc((void**)&b->tables, tables.size() * sizeof(double2)) ||
+      !alloc((void**)&b->segs, segs.size() * sizeof(Seg)) ||
+      !alloc((void**)&b->pptr, pptr.size() * sizeof(int32_t)) ||
+      !alloc((void**)&b->pops, pops.size() * sizeof(int32_t)) ||
       !alloc((void**)&b->coef, ops.size() * sizeof(Rot)) ||
       !alloc((void**)&b->contrib, ops.size() * sizeof(double)) ||
       !alloc((void**)&b->counter, sizeof(int)) || !alloc((void**)&b->theta, P * sizeof(double)) ||
@@ -584,6 +614,9 @@ sv_status sv_batch_create(const sv_instance* inst, int32_t n, void* stream, sv_b
       (e = up(b->ops, ops.data(), ops.size() * sizeof(DOp))) != cudaSuccess ||
       (e = up(b->groups, groups.data(), groups.size() * sizeof(DGroup))) != cudaSuccess ||
       (e = up(b->tables, tables.data(), tables.size() * sizeof(double2))) != cudaSuccess ||
+      (e = up(b->segs, segs.data(), segs.size() * sizeof(Seg))) != cudaSuccess ||
+      (e = up(b->pptr, pptr.data(), pptr.size() * sizeof(int32_t))) != cudaSuccess ||
+      (e = up(b->pops, pops.data(), pops.size() * sizeof(int32_t))) != cudaSuccess ||
       (e = cudaStreamSynchronize(b->stream)) != cudaSuccess ||
       (e = batch_prepare(nmax, &b->grid)) != cudaSuccess) {
     set_error("batch upload failed: %s", cudaGetErrorString(e));
@@ -592,6 +625,14 @@ sv_status sv_batch_create(const sv_instance* inst, int32_t n, void* stream, sv_b
   }
   b->grid = std::min(b->grid, n);
   b->smem = batch_smem_bytes(nmax);
+  b->ckpt_slot = ckpt_slot;
+  if (!alloc((void**)&b->ckpt, (size_t)b->grid * ckpt_slot * sizeof(double2))) {
+    cudaGetLastError();
+    set_error("device allocation of %llu checkpoint bytes failed",
+              (unsigned long long)((size_t)b->grid * ckpt_slot * sizeof(double2)));
+    sv_batch_free(b);
+    return SV_ENOMEM;
+  }
   *out = b;
   return SV_OK;
 }
@@ -612,6 +653,11 @@ static BatchArgs batch_args(sv_batch* b, double* theta, double* energy, double* 
   a.ops = b->ops;
   a.groups = b->groups;
   a.tables = b->tables;
+  a.segs = b->segs;
+  a.pptr = b->pptr;
+  a.pops = b->pops;
+  a.ckpt = b->ckpt;
+  a.ckpt_slot = b->ckpt_slot;
   a.theta = theta;
   a.energy = energy;
   a.grad = grad;

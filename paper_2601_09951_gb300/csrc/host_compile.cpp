@@ -124,6 +124,56 @@ sv_status lower_circuit(const sv_circuit* c, int expect_n, HostCircuit& out) {
   return SV_OK;
 }
 
+int segment_ops(const std::vector<DOp>& ops, int min_layer, int min_diag_rz,
+                std::vector<Seg>& segs) {
+  segs.clear();
+  int ckpt = 0;
+  const int n_ops = (int)ops.size();
+  auto push_gates = [&](int first, int count) {
+    if (count <= 0) return;
+    if (!segs.empty() && segs.back().kind == SEG_GATES &&
+        segs.back().first + segs.back().count == first) {
+      segs.back().count += count;
+    } else {
+      segs.push_back(Seg{SEG_GATES, first, count, -1});
+    }
+  };
+  int l = 0;
+  while (l < n_ops) {
+    const int t = ops[l].type;
+    if (t == SV_GATE_RZ || t == SV_GATE_CZ) {
+      int e = l, n_rz = 0;
+      while (e < n_ops && (ops[e].type == SV_GATE_RZ || ops[e].type == SV_GATE_CZ) &&
+             n_rz + (ops[e].type == SV_GATE_RZ) <= kMaxLayer) {
+        n_rz += ops[e].type == SV_GATE_RZ;
+        ++e;
+      }
+      if (n_rz >= min_diag_rz) segs.push_back(Seg{SEG_DIAG, l, e - l, ckpt++});
+      else push_gates(l, e - l);
+      l = e;
+    } else if (t == SV_GATE_RY || t == SV_GATE_RX) {
+      uint64_t used = 0;
+      int e = l;
+      while (e < n_ops && ops[e].type == t && !(used & (1ull << ops[e].bit0)) &&
+             e - l < kMaxLayer) {
+        used |= 1ull << ops[e].bit0;
+        ++e;
+      }
+      if (e - l >= min_layer) segs.push_back(Seg{SEG_RLAYER, l, e - l, ckpt++});
+      else push_gates(l, e - l);
+      l = e;
+    } else {
+      int e = l;
+      while (e < n_ops && ops[e].type != SV_GATE_RZ && ops[e].type != SV_GATE_CZ &&
+             ops[e].type != SV_GATE_RY && ops[e].type != SV_GATE_RX)
+        ++e;
+      push_gates(l, e - l);
+      l = e;
+    }
+  }
+  return ckpt;
+}
+
 static inline int popc64(uint64_t v) { return __builtin_popcountll(v); }
 
 static uint32_t pext_host(uint64_t v, uint64_t m) {

@@ -13,6 +13,7 @@ namespace svqe {
 
 struct DOp;
 struct DGroup;
+struct Seg;
 
 // Thread-local error message (sv_last_error).
 void set_error(const char* fmt, ...);
@@ -27,6 +28,14 @@ struct HostCircuit {
   std::vector<DOp> ops;
 };
 sv_status lower_circuit(const sv_circuit* c, int expect_n, HostCircuit& out);
+
+// Split a lowered op list into segments for the batched kernel (see Seg).  A run of RZ/CZ
+// becomes SEG_DIAG when it holds at least `min_diag_rz` RZ gates; a run of RY (or RX) gates on
+// distinct qubits becomes SEG_RLAYER when it holds at least `min_layer` gates (and at most
+// kMaxLayer); everything else is SEG_GATES.  Returns the number of checkpoints used.
+constexpr int kMaxLayer = 16;
+int segment_ops(const std::vector<DOp>& ops, int min_layer, int min_diag_rz,
+                std::vector<Seg>& segs);
 
 // A Pauli sum grouped by X mask.  Every group's f(k) = sum_t c_t (-i)^{popc(x&z_t)}
 // (-1)^{popc(z_t&k)} is tabulated over the kz bits of the union zu of its z masks, so that

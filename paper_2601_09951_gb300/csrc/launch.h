@@ -40,12 +40,11 @@ namespace svqe {
 
 // One instance of a compiled batch (device record).
 struct BInst {
-  int32_t n, n_ops, n_groups, n_params;
+  int32_t n, n_ops, n_groups, n_params, n_segs, n_ckpt;
   uint64_t ref;
-  int64_t op_off, grp_off, theta_off;
-  int64_t pad;
+  int64_t op_off, grp_off, theta_off, seg_off, pp_off;
 };
-static_assert(sizeof(BInst) == 56, "BInst layout");
+static_assert(sizeof(BInst) == 72, "BInst layout");
 
 struct BatchArgs {
   const BInst* inst;
@@ -54,11 +53,16 @@ struct BatchArgs {
   const DOp* ops;
   const DGroup* groups;
   const double2* tables;
+  const Seg* segs;
+  const int32_t* pptr;     // per instance n_params+1 offsets into pops (absolute)
+  const int32_t* pops;     // op indices (relative to the instance) using each parameter
   double* theta;           // concatenated parameters (updated in place when n_steps > 0)
   double* energy;          // [n_inst]
   double* grad;            // concatenated gradients
   Rot* coef;               // scratch, one per op
   double* contrib;         // scratch, one per op
+  double2* ckpt;           // scratch, ckpt_slot amplitudes per CTA
+  int64_t ckpt_slot;
   int* counter;            // work-queue head, zeroed before each launch
   int n_steps;             // 0: one evaluation; > 0: that many gradient-descent updates
   double lr;               // step when lr_inst == nullptr

@@ -46,6 +46,25 @@ struct DGroup {
 };
 static_assert(sizeof(DGroup) == 32, "DGroup layout");
 
+// A segment of a circuit's op list, as the batched kernel executes it.
+//   SEG_GATES : ops applied one at a time; the adjoint sweep un-applies each op to psi and
+//               lambda and takes its gradient in between.
+//   SEG_RLAYER: RY (or RX) gates on distinct qubits.  They commute, so every gradient of the
+//               layer is taken from (psi, lambda) at the layer's end; the sweep then
+//               un-applies the layer to lambda only and reloads psi from a checkpoint saved
+//               on the forward pass.
+//   SEG_DIAG  : RZ and CZ gates (diagonal, mutually commuting), applied as one phase
+//               e^{-i sum_q phi_q s_q(k)} (+-1 for CZ) per amplitude from two half tables;
+//               gradients from w_k = Im(conj(lambda_k) psi_k); psi reloaded from a checkpoint.
+enum { SEG_GATES = 0, SEG_RLAYER = 1, SEG_DIAG = 2 };
+struct Seg {
+  int32_t kind;
+  int32_t first;  // first op
+  int32_t count;  // number of ops
+  int32_t ckpt;   // checkpoint slot of psi before the segment, or -1
+};
+static_assert(sizeof(Seg) == 16, "Seg layout");
+
 __host__ __device__ __forceinline__ bool is_param_type(int t) {
   return t == SV_GATE_RX || t == SV_GATE_RY || t == SV_GATE_RZ || t == SV_GATE_SINGLE_EXC ||
          t == SV_GATE_DOUBLE_EXC;

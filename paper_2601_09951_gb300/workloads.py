@@ -20,6 +20,7 @@ a qubit-count scaling study).  The coefficients are synthetic: the real H2/STO-3
 are not part of this project.
 """
 import itertools
+import math
 
 import numpy as np
 
@@ -197,8 +198,9 @@ def uccsd_instance(n=20, n_elec=10, n_singles=80, n_doubles=320, n_terms=2000, s
 
     Hamiltonian of n_terms weight <= 4 strings: I, every Z_i, every Z_iZ_j, then 8-string
     families on seeded p<q<r<s (all X/Y strings with an even number of Y), then X_pX_q+Y_pY_q
-    pairs, topped up with single X_pX_q strings to exactly n_terms.  Coefficients
-    +-1/(1+rank), rank a seeded permutation."""
+    pairs, topped up with single X_pX_q strings to exactly n_terms (fewer on registers too
+    small to hold that many distinct strings).  Coefficients +-1/(1+rank), rank a seeded
+    permutation."""
     rng = _rng(seed)
     occ = list(range(n_elec))
     vir = list(range(n_elec, n))
@@ -226,7 +228,7 @@ def uccsd_instance(n=20, n_elec=10, n_singles=80, n_doubles=320, n_terms=2000, s
     fam8 = [s for s in ("".join(t) for t in itertools.product("XY", repeat=4))
             if s.count("Y") % 2 == 0]
     remaining = n_terms - len(strings)
-    n_quads = min(remaining // 8, 180)
+    n_quads = min(max(remaining, 0) // 8, 180, math.comb(n, 4))
     quads = set()
     while len(quads) < n_quads:
         quads.add(tuple(sorted(int(v) for v in rng.choice(n, size=4, replace=False))))
@@ -234,22 +236,21 @@ def uccsd_instance(n=20, n_elec=10, n_singles=80, n_doubles=320, n_terms=2000, s
         for s in sorted(fam8):
             strings.append(dict(zip(qd, s)))
     remaining = n_terms - len(strings)
-    n_pairs = min(remaining // 2, n * (n - 1) // 2)
+    n_pairs = min(max(remaining, 0) // 2, n * (n - 1) // 2)
     pairs = set()
     while len(pairs) < n_pairs:
         pairs.add(tuple(sorted(int(v) for v in rng.choice(n, size=2, replace=False))))
     for p, q in sorted(pairs):
         strings.append({p: "X", q: "X"})
         strings.append({p: "Y", q: "Y"})
-    while len(strings) < n_terms:
-        p, q = sorted(int(v) for v in rng.choice(n, size=2, replace=False))
-        if (p, q) in pairs:
-            continue
-        pairs.add((p, q))
+    free = [pq for pq in itertools.combinations(range(n), 2) if pq not in pairs]
+    rng.shuffle(free)
+    while len(strings) < n_terms and free:
+        p, q = free.pop()
         strings.append({p: "X", q: "X"})
     strings = strings[:n_terms]
-    rank = rng.permutation(n_terms)
-    sign = rng.choice([-1.0, 1.0], size=n_terms)
+    rank = rng.permutation(len(strings))
+    sign = rng.choice([-1.0, 1.0], size=len(strings))
     terms = [pauli_masks(n, f) + (float(sign[k] / (1.0 + rank[k])),)
              for k, f in enumerate(strings)]
     ref = sum(1 << (n - 1 - q) for q in occ)

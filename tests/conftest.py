@@ -11,3 +11,14 @@ if ROOT not in sys.path:
 def pytest_configure(config):
     config.addinivalue_line("markers", "gpu: needs a CUDA GPU (GB300, sm_103a)")
     config.addinivalue_line("markers", "slow: long-running case")
+
+
+@pytest.fixture(scope="session", autouse=True)
+def _oracle_threads():
+    """Let the oracle's parameter-shift evaluations use every host core."""
+    try:
+        import oracle
+        oracle.set_threads(os.cpu_count() or 1)
+    except Exception:
+        pass
+    yield
