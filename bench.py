@@ -32,8 +32,8 @@ FP64_PEAK_TFLOPS = 2 * 2 * 152 * 2.070e9 / 1e12  # 2 DFMA/clk/SM x 2 flop x 152 
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
-    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--instances", type=int, default=4096)
     ap.add_argument("--seed", type=int, default=1002)
@@ -56,30 +56,6 @@ def config(args, world):
             "ansatz": "RY+RZ on all qubits + CNOT ladder per layer",
             "l2": "flushed between timed steps (256 MiB write)",
             "parallelism": f"replicas{world}"}
-
-
-def algorithmic_fp64_flops(insts):
-    """FP64 flops (FMA = 2) of one energy + adjoint-gradient pass, counted from the kernel's
-    arithmetic: lifting rotations 12 flop per pair (6 DFMA), gradient inner product 7 flop per
-    pair (1 DMUL + 3 DFMA) plus 1 DADD, H 8 flop per pair, group tables 4 flop per amplitude
-    (real or imaginary) or 8 (complex), energy 4 flop per amplitude."""
-    from paper_2601_09951_gb300 import svqe
-    from paper_2601_09951_gb300 import workloads as W
-    total = 0.0
-    for inst in insts:
-        c = inst["circuit"]
-        n = int(c["n"])
-        N = 1 << n
-        for t, p in zip(c["types"], c["params"]):
-            t = int(t)
-            pairs = {W.SINGLE_EXC: N // 4, W.DOUBLE_EXC: N // 16}.get(t, N // 2)
-            if t in (W.RX, W.RY, W.RZ, W.SINGLE_EXC, W.DOUBLE_EXC):
-                total += pairs * (12 + 24 + (8 if p >= 0 else 0))
-            elif t == W.H:
-                total += pairs * (8 + 16)
-        _, _, cls, _, _ = svqe.ham_lower(inst["ham"], n, 12)
-        total += N * (4 * np.sum(cls < 2) + 8 * np.sum(cls == 2) + 4)
-    return total
 
 
 class ClockSampler:
@@ -274,7 +250,7 @@ def main():
         if dist is not None:
             dist.destroy_process_group()
         return
-    flops = algorithmic_fp64_flops(insts)
+    flops, hbm_bytes = batch.cost()
     kernel_s = dev_s / args.steps
     achieved = flops / kernel_s / 1e12
     line = {
@@ -290,7 +266,7 @@ def main():
                      "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,
                      "kernel": "k_batch", "what": "FP64 pipe (2 DFMA/clk/SM x 152 SMs x "
                      "2.07 GHz); algorithmic FP64 flops per launch / mean launch time",
-                     "flops_per_launch": flops},
+                     "flops_per_launch": flops, "hbm_bytes_per_launch": hbm_bytes},
         "clocks": clocks,
         "wall_s_incl_l2_flush": wall,
     }

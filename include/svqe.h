@@ -198,6 +198,11 @@ sv_status sv_batch_create(const sv_instance* inst, int32_t n, void* cuda_stream,
 sv_status sv_batch_free(sv_batch* b);
 /* Sizes: instances, total parameters. */
 sv_status sv_batch_info(const sv_batch* b, int32_t* n_instances, int64_t* n_params_total);
+/* Algorithmic cost of one sv_batch_run, counted from the compiled segments exactly as the
+ * kernel executes them: fp64_flops (FMA = 2) of the forward pass, lambda = H psi and the
+ * adjoint sweep; hbm_bytes read and written (program, tables, parameters, results,
+ * checkpoints).  Either pointer may be NULL.  Host-only. */
+sv_status sv_batch_cost(const sv_batch* b, double* fp64_flops, double* hbm_bytes);
 /* Energy and adjoint gradient of every instance, host buffers: theta (n_params_total) is
  * copied in, energy (n) and grad (n_params_total) are copied out; synchronises. */
 sv_status sv_batch_run(sv_batch* b, const double* theta, double* energy, double* grad);

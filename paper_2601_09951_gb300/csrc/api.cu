@@ -80,6 +80,8 @@ struct sv_batch {
   double* theta = nullptr;   // owned buffers for the host-pointer entry point
   double* energy = nullptr;
   double* grad = nullptr;
+  double flops = 0.0;        // algorithmic FP64 flops of one run (sv_batch_cost)
+  double bytes = 0.0;        // algorithmic HBM bytes of one run
   // CUDA graph of [counter reset, persistent kernel] for one set of device pointers
   cudaGraphExec_t exec = nullptr;
   const void* key[3] = {nullptr, nullptr, nullptr};
@@ -478,6 +480,39 @@ sv_status sv_state_device_ptr(sv_ctx* c, void** psi_dev) {
 // ------------------------------------------------------------------------------ batches
 static constexpr int kTableBitsBatch = SV_BATCH_MAX_QUBITS;  // full diagonal tables allowed
 
+// FP64 flops (FMA = 2) of one instance's forward pass, lambda = H psi and adjoint sweep, as
+// k_batch executes its segments: lifting rotation 12 per pair, gradient 8 per pair, H gate 8
+// per pair; a diagonal segment 12 per amplitude forward and 16 + (RZ gates on bits >= 8)
+// backward; a commuting layer un-applies lambda only; groups 4 (real or imaginary table) or 8
+// (complex) per amplitude plus 4 for the energy.
+static double batch_instance_flops(const HostCircuit& hc, const HostHam& hh,
+                                   const std::vector<Seg>& segs) {
+  const double N = (double)(1u << hc.n);
+  double f = 0.0;
+  for (const Seg& s : segs) {
+    for (int l = s.first; l < s.first + s.count; ++l) {
+      const DOp& op = hc.ops[l];
+      const double pairs = N / (double)(1u << op.k);
+      const bool rot = is_param_type(op.type);
+      if (s.kind == SEG_GATES) {
+        if (rot) f += pairs * (12 + 24 + (op.param >= 0 ? 8 : 0));
+        else if (op.type == SV_GATE_H) f += pairs * (8 + 16);
+      } else if (s.kind == SEG_RLAYER) {
+        f += pairs * (12 + 8 + 12);
+      }
+    }
+    if (s.kind == SEG_DIAG) {
+      int hi = 0;
+      for (int l = s.first; l < s.first + s.count; ++l)
+        if (hc.ops[l].type == SV_GATE_RZ && hc.ops[l].bit0 >= 8) ++hi;
+      f += N * (12 + 16 + hi);
+    }
+  }
+  for (const DGroup& g : hh.groups) f += N * (g.cls == 2 ? 8 : 4);
+  f += N * 4;
+  return f;
+}
+
 sv_status sv_batch_free(sv_batch* b) {
   if (!b) return SV_OK;
   cudaSetDevice(b->device);
@@ -515,6 +550,7 @@ sv_status sv_batch_create(const sv_instance* inst, int32_t n, void* stream, sv_b
   std::vector<Seg> segs;
   std::vector<int32_t> pptr, pops;
   std::vector<double> cost(n);
+  double flops = 0.0, bytes = 0.0;
   int nmax = 1;
   int64_t theta_off = 0, ckpt_slot = 1;
   for (int i = 0; i < n; ++i) {
@@ -532,6 +568,11 @@ sv_status sv_batch_create(const sv_instance* inst, int32_t n, void* stream, sv_b
     if (I.ref >= (1ull << hc.n)) { set_error("instance %d: reference index out of range", i); return SV_EINVAL; }
     std::vector<Seg> sg;
     const int n_ckpt = segment_ops(hc.ops, 2, 3, sg);
+    flops += batch_instance_flops(hc, hh, sg);
+    bytes += (double)hc.ops.size() * (sizeof(DOp) + sizeof(Rot) * 2 + 2 * sizeof(double)) +
+             (double)hh.groups.size() * sizeof(DGroup) +
+             (double)hh.tables.size() * sizeof(double2) + 3.0 * 8 * hc.n_params + 8 +
+             2.0 * n_ckpt * sizeof(double2) * (double)(1u << hc.n);
     BInst& B = bi[i];
     B.n = hc.n;
     B.n_ops = (int)hc.ops.size();
@@ -571,6 +612,8 @@ sv_status sv_batch_create(const sv_instance* inst, int32_t n, void* stream, sv_b
   if (!b) { set_error("host allocation failed"); return SV_ENOMEM; }
   b->n_inst = n;
   b->nmax = nmax;
+  b->flops = flops;
+  b->bytes = bytes;
   b->total_params = theta_off;
   b->total_ops = (int64_t)ops.size();
   cudaGetDevice(&b->device);
@@ -634,6 +677,13 @@ sv_status sv_batch_create(const sv_instance* inst, int32_t n, void* stream, sv_b
     return SV_ENOMEM;
   }
   *out = b;
+  return SV_OK;
+}
+
+sv_status sv_batch_cost(const sv_batch* b, double* fp64_flops, double* hbm_bytes) {
+  if (!b) { set_error("NULL handle"); return SV_EINVAL; }
+  if (fp64_flops) *fp64_flops = b->flops;
+  if (hbm_bytes) *hbm_bytes = b->bytes;
   return SV_OK;
 }
 

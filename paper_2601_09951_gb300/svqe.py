@@ -88,6 +88,7 @@ def lib():
         "sv_batch_create": ([P, i32, P, P], i32),
         "sv_batch_free": ([P], i32),
         "sv_batch_info": ([P, P, P], i32),
+        "sv_batch_cost": ([P, P, P], i32),
         "sv_batch_run": ([P, P, P, P], i32),
         "sv_batch_run_dev": ([P, P, P, P], i32),
         "sv_batch_vqe_dev": ([P, P, dbl, i32, P], i32),
@@ -298,6 +299,12 @@ class Batch:
         ni, npar = ctypes.c_int32(), ctypes.c_int64()
         _check(lib().sv_batch_info(self._b, ctypes.byref(ni), ctypes.byref(npar)))
         self.n_instances, self.n_params = ni.value, npar.value
+
+    def cost(self):
+        """(FP64 flops, HBM bytes) of one run, from the compiled segments."""
+        f, b = ctypes.c_double(), ctypes.c_double()
+        _check(lib().sv_batch_cost(self._b, ctypes.byref(f), ctypes.byref(b)))
+        return f.value, b.value
 
     def theta_of(self, instances):
         return np.concatenate([np.asarray(i["theta"], np.float64) for i in instances]) \

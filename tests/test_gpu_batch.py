@@ -99,3 +99,12 @@ def test_on_device_gradient_descent_h2():
             assert_energy(traj[t, i], e0, inst["ham"], f"{inst['name']} step {t}")
             assert_grad((before[i:i + 1] - after[i:i + 1]) / lr, g0, inst["ham"])
     assert np.array_equal(th.cpu().numpy(), th1.cpu().numpy())
+
+
+def test_cost_model_counts_by_hand():
+    """One H2 instance: DoubleExcitation on 16 amplitudes is 1 pair (12 forward + 24 un-apply
+    + 8 gradient flops); two real groups (x = 0 with 11 terms, x = 1111 with 4 two-Y strings)
+    at 4 flops per amplitude each, plus 4 per amplitude for the energy: 44 + 128 + 64."""
+    b = svqe.Batch(W.h2_sweep(1))
+    flops, _ = b.cost()
+    assert flops == 44 + 2 * 16 * 4 + 16 * 4
