@@ -41,6 +41,9 @@ struct sv_ctx {
   size_t theta_cap = 0, grad_cap = 0;
   double* etraj = nullptr;
   size_t etraj_cap = 0;
+  FItem* items = nullptr;     // fused-pass items of the staged circuit
+  size_t items_cap = 0;
+  HostPlan plan;              // fused passes of the staged circuit (empty: per-op kernels)
 };
 
 struct sv_ham {
@@ -180,7 +183,7 @@ sv_status sv_create(sv_ctx** out, int32_t n, void* stream) {
     return SV_ENOMEM;
   }
   c->ref = 0;
-  if (launch_init_basis(c->psi, n, 0, c->stream) != cudaSuccess) {
+  if (fused_prepare() != cudaSuccess || launch_init_basis(c->psi, n, 0, c->stream) != cudaSuccess) {
     set_error("init kernel launch failed");
     sv_destroy(c);
     return SV_ECUDA;
@@ -204,6 +207,7 @@ sv_status sv_destroy(sv_ctx* c) {
   cudaFree(c->theta);
   cudaFree(c->grad);
   cudaFree(c->etraj);
+  cudaFree(c->items);
   if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
   cudaGetLastError();
   delete c;
@@ -321,12 +325,25 @@ static sv_status stage_circuit(sv_ctx* c, const HostCircuit& hc) {
   if (n_ops)
     SV_CUDA(cudaMemcpyAsync(c->ops, hc.ops.data(), n_ops * sizeof(DOp), cudaMemcpyHostToDevice,
                             c->stream), c);
+  c->plan.passes.clear();
+  c->plan.items.clear();
+  if (c->n >= kFusedMinQubits && n_ops > 0) {
+    plan_passes(hc.ops, c->n, fused_tile_bits(), c->plan);
+    SV_CUDA(grow(c->items, c->items_cap, c->plan.items.size()), c);
+    SV_CUDA(cudaMemcpyAsync(c->items, c->plan.items.data(), c->plan.items.size() * sizeof(FItem),
+                            cudaMemcpyHostToDevice, c->stream), c);
+  }
   return SV_OK;
 }
 
 static sv_status forward(sv_ctx* c, const HostCircuit& hc, const double* theta_dev) {
   const int n_ops = (int)hc.ops.size();
   SV_CUDA(launch_prep_coefs(c->ops, n_ops, theta_dev, c->coef, c->stream), c);
+  if (!c->plan.passes.empty()) {
+    for (const FPass& P : c->plan.passes)
+      SV_CUDA(launch_fpass(c->psi, P, c->items, c->ops, c->coef, theta_dev, c->stream), c);
+    return SV_OK;
+  }
   for (int l = 0; l < n_ops; ++l)
     SV_CUDA(launch_apply_op(c->psi, c->n, hc.ops[l], c->coef + l, false, c->stream), c);
   return SV_OK;
@@ -343,10 +360,16 @@ static sv_status adjoint_core(sv_ctx* c, const HostCircuit& hc, const sv_ham* H,
                       c->stream), c);
   SV_CUDA(launch_sum(c->epart, kRedBlocks, energy_dev, c->stream), c);
   const int n_ops = (int)hc.ops.size();
-  for (int l = n_ops - 1; l >= 0; --l) {
-    const DOp& op = hc.ops[l];
-    double* part = op.param >= 0 ? c->gpart + (size_t)l * kRedBlocks : nullptr;
-    SV_CUDA(launch_adjoint_op(c->psi, c->lam, c->n, op, c->coef + l, part, c->stream), c);
+  if (!c->plan.passes.empty()) {
+    for (int p = (int)c->plan.passes.size() - 1; p >= 0; --p)
+      SV_CUDA(launch_bpass(c->psi, c->lam, c->plan.passes[p], c->items, c->ops, c->coef,
+                           theta_dev, c->gpart, c->stream), c);
+  } else {
+    for (int l = n_ops - 1; l >= 0; --l) {
+      const DOp& op = hc.ops[l];
+      double* part = op.param >= 0 ? c->gpart + (size_t)l * kRedBlocks : nullptr;
+      SV_CUDA(launch_adjoint_op(c->psi, c->lam, c->n, op, c->coef + l, part, c->stream), c);
+    }
   }
   SV_CUDA(launch_reduce_grads(c->ops, n_ops, c->gpart, hc.n_params, c->contrib, grad_dev,
                               c->stream), c);

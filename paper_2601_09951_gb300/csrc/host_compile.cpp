@@ -174,6 +174,114 @@ int segment_ops(const std::vector<DOp>& ops, int min_layer, int min_diag_rz,
   return ckpt;
 }
 
+namespace {
+struct Unit {      // a schedulable unit: one op, or a run of RZ ops (diagonal item)
+  int kind;        // 0 op, 1 diag
+  int first, count;
+  uint64_t pair;   // bits that must lie inside the tile
+  uint64_t touch;  // bits the unit acts on
+  int slots;       // gradient slots it needs
+};
+}  // namespace
+
+void plan_passes(const std::vector<DOp>& ops, int n, int m, HostPlan& plan) {
+  plan.passes.clear();
+  plan.items.clear();
+  std::vector<Unit> units;
+  const int n_ops = (int)ops.size();
+  for (int l = 0; l < n_ops;) {
+    if (ops[l].type == SV_GATE_RZ) {
+      int e = l;
+      while (e < n_ops && ops[e].type == SV_GATE_RZ && e - l < kMaxSlots) ++e;
+      if (e - l >= 3) {
+        Unit u{1, l, e - l, 0, 0, 0};
+        for (int q = l; q < e; ++q) {
+          u.touch |= 1ull << ops[q].bit0;
+          u.slots += ops[q].param >= 0;
+        }
+        units.push_back(u);
+        l = e;
+        continue;
+      }
+    }
+    const DOp& op = ops[l];
+    uint64_t bits = 0;
+    for (int a = 0; a < op.k; ++a) bits |= 1ull << op.sb[a];
+    units.push_back(Unit{0, l, 1, bits, bits, op.param >= 0 ? 1 : 0});
+    ++l;
+  }
+  m = std::min(m, n);
+  const uint64_t low = (1ull << std::min(kMinLowBits, n)) - 1ull;
+  std::vector<char> done(units.size(), 0);
+  size_t left = units.size();
+  while (left > 0) {
+    uint64_t pair = 0, blocked = 0;
+    int slots = 0;
+    bool have_diag = false;
+    std::vector<int> take;
+    for (size_t u = 0; u < units.size(); ++u) {
+      if (done[u]) continue;
+      const Unit& U = units[u];
+      bool ok = !(U.touch & blocked) && __builtin_popcountll(pair | U.pair | low) <= m &&
+                slots + U.slots <= kMaxSlots && !(U.kind == 1 && have_diag);
+      if (!ok) {
+        blocked |= U.touch;
+        continue;
+      }
+      take.push_back((int)u);
+      pair |= U.pair;
+      slots += U.slots;
+      have_diag |= U.kind == 1;
+    }
+    // Tile bits: the pass's pair bits plus the lowest free bits up to m (contiguous runs).
+    uint64_t tile = pair;
+    for (int b = 0; b < n && __builtin_popcountll(tile) < m; ++b) tile |= 1ull << b;
+    int c = 0;
+    while (c < n && (tile >> c & 1ull)) ++c;
+    FPass P{};
+    P.tile_mask = tile;
+    P.outer_mask = ((n == 64) ? ~0ull : ((1ull << n) - 1ull)) & ~tile;
+    P.m = __builtin_popcountll(tile);
+    P.c = c;
+    P.first_item = (int)plan.items.size();
+    P.n_items = (int)take.size();
+    int slot = 0;
+    for (int u : take) {
+      const Unit& U = units[u];
+      FItem it{};
+      it.kind = U.kind;
+      it.op = U.first;
+      it.count = U.count;
+      it.slot = U.slots ? slot : -1;
+      slot += U.slots;
+      if (U.kind == 0) {
+        // translate the op to tile-local bit positions
+        auto loc = [&](uint64_t v) {
+          uint64_t r = 0;
+          int k = 0;
+          for (int b = 0; b < n; ++b)
+            if (tile >> b & 1ull) {
+              if (v >> b & 1ull) r |= 1ull << k;
+              ++k;
+            }
+          return r;
+        };
+        DOp L = ops[U.first];
+        L.bit0 = __builtin_ctzll(loc(1ull << ops[U.first].bit0));
+        for (int a = 0; a < L.k; ++a) L.sb[a] = (uint8_t)__builtin_ctzll(loc(1ull << L.sb[a]));
+        L.lo_or = loc(L.lo_or);
+        L.flip = loc(L.flip);
+        it.local = L;
+      }
+      plan.items.push_back(it);
+      done[u] = 1;
+      --left;
+    }
+    P.n_slots = slot;
+    plan.passes.push_back(P);
+  }
+}
+
 static inline int popc64(uint64_t v) { return __builtin_popcountll(v); }
 
 static uint32_t pext_host(uint64_t v, uint64_t m) {

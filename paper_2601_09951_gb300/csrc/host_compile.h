@@ -8,12 +8,15 @@
 #include <vector>
 
 #include "../../include/svqe.h"
+#include "svqe_types.h"
 
 namespace svqe {
 
 struct DOp;
 struct DGroup;
 struct Seg;
+struct FPass;
+struct FItem;
 
 // Thread-local error message (sv_last_error).
 void set_error(const char* fmt, ...);
@@ -36,6 +39,18 @@ sv_status lower_circuit(const sv_circuit* c, int expect_n, HostCircuit& out);
 constexpr int kMaxLayer = 16;
 int segment_ops(const std::vector<DOp>& ops, int min_layer, int min_diag_rz,
                 std::vector<Seg>& segs);
+
+// Plan the fused passes of an n-qubit circuit with tiles of m bits (see FPass): ops are taken
+// greedily in order into the current pass while the pass's pair bits fit the tile; an op may
+// move ahead of ops skipped for this pass only if it shares no qubit with them (so it
+// commutes with them).  Runs of >= 3 consecutive RZ gates become one diagonal item (at most
+// one per pass, at most kMaxSlots RZ gates).  A pass holds at most kMaxSlots gradient slots.
+constexpr int kMaxSlots = kMaxSlotsDev;
+struct HostPlan {
+  std::vector<FPass> passes;
+  std::vector<FItem> items;
+};
+void plan_passes(const std::vector<DOp>& ops, int n, int m, HostPlan& plan);
 
 // A Pauli sum grouped by X mask.  Every group's f(k) = sum_t c_t (-i)^{popc(x&z_t)}
 // (-1)^{popc(z_t&k)} is tabulated over the kz bits of the union zu of its z masks, so that

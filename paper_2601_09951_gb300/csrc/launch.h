@@ -38,6 +38,19 @@ cudaError_t launch_gd_update(double* theta, const double* grad, int n, double lr
 
 namespace svqe {
 
+// Fused passes of the single-state path (k_fused.cu).  Tiles of fused_tile_bits() bits;
+// used for registers of at least kFusedMinQubits qubits.
+constexpr int kFusedMinQubits = 14;
+int fused_tile_bits();
+cudaError_t fused_prepare();
+cudaError_t launch_fpass(double2* psi, const FPass& P, const FItem* items, const DOp* gops,
+                         const Rot* coef, const double* theta, cudaStream_t s);
+// Backward pass: partial[op * kRedBlocks + b] receives block b's gradient share of every
+// parameterised op of the pass.
+cudaError_t launch_bpass(double2* psi, double2* lam, const FPass& P, const FItem* items,
+                         const DOp* gops, const Rot* coef, const double* theta, double* partial,
+                         cudaStream_t s);
+
 // One instance of a compiled batch (device record).
 struct BInst {
   int32_t n, n_ops, n_groups, n_params, n_segs, n_ckpt;

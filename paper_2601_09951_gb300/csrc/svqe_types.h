@@ -65,6 +65,38 @@ struct Seg {
 };
 static_assert(sizeof(Seg) == 16, "Seg layout");
 
+// Gradient slots per fused pass (and RZ gates per diagonal item).
+constexpr int kMaxSlotsDev = 16;
+// Lowest contiguous bits every fused tile includes (runs of 2^kMinLowBits amplitudes).
+constexpr int kMinLowBits = 4;
+
+// A fused pass of the single-state path: every item of the pass acts inside one "tile" of
+// 2^m amplitudes (the basis-index bits in tile_mask, which always include the c lowest bits,
+// so a tile is 2^(m-c) contiguous runs of 2^c amplitudes); the other bits (outer_mask) number
+// the 2^(n-m) tiles.  A pass loads a tile into shared memory, applies its items in order and
+// writes it back, so a whole run of gates costs one read and one write of the state.
+struct FPass {
+  uint64_t tile_mask;
+  uint64_t outer_mask;
+  int32_t m, c;
+  int32_t first_item, n_items;
+  int32_t n_slots;  // gradient slots used by the pass's parameterised items
+  int32_t pad[3];
+};
+static_assert(sizeof(FPass) == 48, "FPass layout");
+
+// One item of a fused pass: an op in tile-local bit coordinates (kind 0), or a run of RZ gates
+// applied as one diagonal phase (kind 1: global ops [op, op + count); their bits may lie
+// inside or outside the tile).  slot: first gradient slot of the item, or -1.
+struct FItem {
+  int32_t kind;
+  int32_t op;
+  int32_t count;
+  int32_t slot;
+  DOp local;
+};
+static_assert(sizeof(FItem) == 64, "FItem layout");
+
 __host__ __device__ __forceinline__ bool is_param_type(int t) {
   return t == SV_GATE_RX || t == SV_GATE_RY || t == SV_GATE_RZ || t == SV_GATE_SINGLE_EXC ||
          t == SV_GATE_DOUBLE_EXC;

@@ -1,0 +1,108 @@
+"""GPU parity of the fused shared-memory passes (registers of >= 14 qubits): gates staged in
+tiles of 2^11 amplitudes with the low bits contiguous and the other bits strided, diagonal RZ
+runs applied from half tables with factors for RZ gates on bits outside the tile, and the
+adjoint sweep's per-thread gradient slots."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2601_09951_gb300 import svqe
+from paper_2601_09951_gb300 import workloads as W
+from tests.parity import PSI_TOL, assert_energy, assert_grad
+
+pytestmark = pytest.mark.gpu
+
+
+def _rand_state(n, rng):
+    v = rng.normal(size=1 << n) + 1j * rng.normal(size=1 << n)
+    return v / np.linalg.norm(v)
+
+
+def test_single_gates_on_high_middle_and_low_wires():
+    n = 15
+    rng = np.random.default_rng(1)
+    ctx = svqe.Context(n)
+    cases = []
+    for q in (0, 1, 6, 10, 11, 13, 14):
+        for g in (W.X, W.H, W.RX, W.RY, W.RZ):
+            cases.append((g, [q]))
+    for a, b in ((0, 14), (14, 0), (3, 9), (12, 13), (1, 2)):
+        for g in (W.CNOT, W.CZ, W.SINGLE_EXC):
+            cases.append((g, [a, b]))
+    for w in ((0, 1, 2, 3), (14, 0, 7, 9), (11, 12, 13, 14), (5, 2, 13, 0)):
+        cases.append((W.DOUBLE_EXC, list(w)))
+    for gtype, wires in cases:
+        psi = _rand_state(n, rng)
+        t = rng.uniform(-7, 7)
+        cb = W.CircuitBuilder(n)
+        param = gtype in (W.RX, W.RY, W.RZ, W.SINGLE_EXC, W.DOUBLE_EXC)
+        cb.add(gtype, wires, param="new" if param else None)
+        circ = cb.build()
+        ctx.set_state(psi)
+        ctx.apply_circuit(circ, np.array([t]) if param else np.zeros(0))
+        got = ctx.get_state()
+        want = oracle.apply_gate(psi, n, gtype, wires, t)
+        assert np.max(np.abs(got - want)) <= PSI_TOL, (W.GATE_NAMES[gtype], wires)
+
+
+def test_rz_runs_across_tile_and_outer_bits():
+    n = 16
+    rng = np.random.default_rng(2)
+    cb = W.CircuitBuilder(n)
+    for q in range(n):
+        cb.add(W.H, (q,))
+    for q in rng.permutation(n):
+        cb.add(W.RZ, (int(q),), param="new")
+    for q in range(0, n, 3):
+        cb.add(W.RY, (q,), param="new")
+    for q in (15, 0, 7, 8, 3):
+        cb.add(W.RZ, (q,), param="new")
+    circ = cb.build()
+    theta = rng.uniform(-np.pi, np.pi, circ["n_params"])
+    inst = {"circuit": circ, "ham": W.random_pauli_sum(rng, n, 40, 0.5, 5, 1.0), "ref": 0,
+            "theta": theta}
+    ctx = svqe.Context(n)
+    ctx.init_reference(0)
+    ctx.apply_circuit(circ, theta)
+    want = oracle.state(circ, theta, 0)
+    assert np.max(np.abs(ctx.get_state() - want)) <= PSI_TOL
+    H = svqe.Ham(ctx, inst["ham"])
+    e, g = ctx.adjoint_grad(circ, theta, H)
+    e0, g0 = oracle.energy_grad(inst)
+    assert_energy(e, e0, inst["ham"])
+    assert_grad(g, g0, inst["ham"])
+
+
+@pytest.mark.parametrize("make", [
+    lambda: W.hea_instance(16, 2, 60, 31, ring=True),
+    lambda: W.hea_instance(14, 3, 80, 32),
+    lambda: W.uccsd_instance(n=16, n_elec=8, n_singles=16, n_doubles=24, n_terms=300, seed=33),
+])
+def test_adjoint_through_fused_passes(make):
+    inst = make()
+    n = inst["circuit"]["n"]
+    ctx = svqe.Context(n)
+    ctx.init_reference(inst["ref"])
+    H = svqe.Ham(ctx, inst["ham"])
+    e, g = ctx.adjoint_grad(inst["circuit"], inst["theta"], H)
+    e0, g0 = oracle.energy_grad(inst)
+    assert_energy(e, e0, inst["ham"], inst["name"])
+    assert_grad(g, g0, inst["ham"], inst["name"])
+
+
+def test_fused_and_per_op_paths_agree_on_the_state():
+    """The same 16-qubit circuit applied as one circuit (fused passes) and gate by gate
+    (one-gate circuits, which the planner turns into one-item passes)."""
+    inst = W.hea_instance(16, 3, 10, 34, ring=True)
+    circ = inst["circuit"]
+    ctx = svqe.Context(16)
+    ctx.init_reference(0)
+    ctx.apply_circuit(circ, inst["theta"])
+    fused = ctx.get_state()
+    ctx.init_reference(0)
+    for gi in range(len(circ["types"])):
+        one = {"n": 16, "types": circ["types"][gi:gi + 1], "wires": circ["wires"][gi:gi + 1],
+               "params": circ["params"][gi:gi + 1], "fixed": circ["fixed"][gi:gi + 1],
+               "n_params": circ["n_params"]}
+        ctx.apply_circuit(one, inst["theta"])
+    np.testing.assert_allclose(ctx.get_state(), fused, atol=PSI_TOL)
