@@ -216,6 +216,53 @@ sv_status sv_batch_run_dev(sv_batch* b, const double* theta_dev, double* energy_
 sv_status sv_batch_vqe_dev(sv_batch* b, double* theta_dev, double lr, int32_t n_steps,
                            double* energy_traj_dev);
 
+/* ---------------------------------------------------------------- no device allocation */
+
+/* This entry point has no counterpart in the paper; it exists for callers that cannot
+ * allocate device memory.  Those are programs whose host application owns every byte of
+ * device memory (a framework's caching allocator, or a fixed budget reserved at start-up) and
+ * forbids allocations by anyone else, and latency-critical loops that must not pay for, or
+ * risk the failure of, a cudaMalloc after start-up.  The caller brings every input and output
+ * buffer; the working memory (psi, lambda, op records, rotation coefficients, reduction
+ * partials) lives in one fixed array of SV_NOALLOC_SCRATCH_BYTES inside the library, which
+ * every GPU that loads the library holds until the process exits.  The call allocates no
+ * device memory and makes no allocating library call.
+ *
+ * sv_adjoint_grad_noalloc computes the same energy and gradient as sv_adjoint_grad_dev, for
+ * states of at most SV_NOALLOC_MAX_QUBITS qubits and circuits of at most
+ * SV_NOALLOC_MAX_GATES gates; larger requests are rejected with SV_EINVAL and a message
+ * naming the limit.
+ *   circuit     host gate records (validated as for sv_apply_circuit).
+ *   ref         basis index of the reference state, < 2^n.
+ *   groups_dev  device array of n_groups sv_group records and tables_dev the device array of
+ *               interleaved complex128 table entries, both as sv_ham_lower reports them for
+ *               the Hamiltonian (x_mask, z_union, z_bits = popcount(z_union), cls,
+ *               table_offset).
+ *   theta_dev   device array of circuit->n_params angles.
+ *   energy_dev  device address receiving E; grad_dev device array of n_params derivatives.
+ *   cuda_stream cudaStream_t to order the work on (NULL: the legacy default stream).
+ * Stream-ordered; returns without synchronising.  The first call on a device looks up the
+ * array's device address once (cudaGetSymbolAddress with that device current); make that
+ * first call before any stream capture.  Every call on a device shares the one array and
+ * leaves its contents behind; calls whose work overlaps on the GPU (other streams or other
+ * threads) race on it, so the caller must order them. */
+typedef struct {
+  uint64_t x_mask;
+  uint64_t z_union;
+  int32_t z_bits;
+  int32_t cls;
+  int64_t table_offset;
+} sv_group;
+
+#define SV_NOALLOC_MAX_QUBITS 14
+#define SV_NOALLOC_MAX_GATES 256
+#define SV_NOALLOC_SCRATCH_BYTES (3u << 20)
+
+sv_status sv_adjoint_grad_noalloc(const sv_circuit* circuit, uint64_t ref,
+                                  const sv_group* groups_dev, int32_t n_groups,
+                                  const double* tables_dev, const double* theta_dev,
+                                  double* energy_dev, double* grad_dev, void* cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

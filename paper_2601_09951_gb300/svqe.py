@@ -92,6 +92,7 @@ def lib():
         "sv_batch_run": ([P, P, P, P], i32),
         "sv_batch_run_dev": ([P, P, P, P], i32),
         "sv_batch_vqe_dev": ([P, P, dbl, i32, P], i32),
+        "sv_adjoint_grad_noalloc": ([P, u64, P, i32, P, P, P, P, P], i32),
     }
     for name, (args, res) in sigs.items():
         fn = getattr(L, name)
@@ -166,6 +167,34 @@ def ham_lower(ham, n, kmax):
     _check(lib().sv_ham_lower(ps.ref(), int(kmax), ctypes.byref(ng), ctypes.byref(nt),
                               _ptr(x), _ptr(zu), _ptr(cls), _ptr(toff), _ptr(table)))
     return x, zu, cls, toff, table[:nt.value]
+
+
+GROUP_DTYPE = np.dtype([("x_mask", "<u8"), ("z_union", "<u8"), ("z_bits", "<i4"),
+                        ("cls", "<i4"), ("table_offset", "<i8")])
+assert GROUP_DTYPE.itemsize == 32
+NOALLOC_MAX_QUBITS = 14
+NOALLOC_MAX_GATES = 256
+
+
+def group_records(ham, n, kmax=14):
+    """(sv_group records, complex128 tables) of a Hamiltonian, from the host-only lowering,
+    for callers that place them in device memory of their own."""
+    x, zu, cls, toff, table = ham_lower(ham, n, kmax)
+    rec = np.zeros(len(x), dtype=GROUP_DTYPE)
+    rec["x_mask"], rec["z_union"], rec["cls"], rec["table_offset"] = x, zu, cls, toff
+    rec["z_bits"] = [bin(int(v)).count("1") for v in zu]
+    return rec, np.ascontiguousarray(table, dtype=np.complex128)
+
+
+def adjoint_grad_noalloc(circuit, ref, groups_ptr, n_groups, tables_ptr, theta_ptr, energy_ptr,
+                         grad_ptr, stream=None):
+    """sv_adjoint_grad_noalloc: every pointer is a device address the caller owns; the
+    library allocates no device memory.  Stream-ordered (synchronise before reading)."""
+    C = circuit if isinstance(circuit, Circuit) else Circuit(circuit)
+    _check(lib().sv_adjoint_grad_noalloc(
+        C.ref(), int(ref), ctypes.c_void_p(groups_ptr), int(n_groups),
+        ctypes.c_void_p(tables_ptr), ctypes.c_void_p(theta_ptr), ctypes.c_void_p(energy_ptr),
+        ctypes.c_void_p(grad_ptr), ctypes.c_void_p(stream) if stream else None))
 
 
 class Ham:
