@@ -141,8 +141,9 @@ sv_status sv_ham_info(const sv_ham* h, int32_t* n_groups, uint64_t* device_bytes
  * gets a table of its own z-weight), fills n_groups and n_table and,
  * when the array pointers are non-NULL (sized from a first call with NULL arrays), the
  * groups (x, zu, cls, toff) and the tables as interleaved (re, im) doubles.  Group g maps
- * (H psi)[k] += table[toff_g + pext(k, zu_g)] * psi[k ^ x_g]; cls is 0 (real table),
- * 1 (imaginary) or 2 (complex). */
+ * (H psi)[k] += f_g(k) * psi[k ^ x_g] with f_g(k) = table[toff_g + pext(k, zu_g)] and cls 0
+ * (real table), 1 (imaginary) or 2 (complex); or, for a group of one term, cls 4 (real) or 5
+ * (imaginary) and f_g(k) = table[toff_g] * (-1)^{popc(zu_g & k)}, zu_g being its z mask. */
 sv_status sv_ham_lower(const sv_paulisum* h, int32_t kmax, int32_t* n_groups, int64_t* n_table,
                        uint64_t* x, uint64_t* zu, int32_t* cls, int64_t* toff, double* table);
 

@@ -10,6 +10,7 @@
 #include <vector>
 
 #include "../../include/svqe.h"
+#include "api_internal.h"
 #include "host_compile.h"
 #include "launch.h"
 #include "svqe_types.h"
@@ -68,7 +69,8 @@ struct sv_batch {
   int grid = 0;
   size_t smem = 0;
   BInst* inst = nullptr;
-  int32_t* order = nullptr;
+  BItem* items = nullptr;
+  int n_items = 0;
   DOp* ops = nullptr;
   DGroup* groups = nullptr;
   double2* tables = nullptr;
@@ -120,8 +122,6 @@ static cudaError_t grow(T*& p, size_t& cap, size_t need) {
   if (e == cudaSuccess) cap = c;
   return e;
 }
-
-extern "C" {
 
 const char* sv_status_str(sv_status s) {
   switch (s) {
@@ -314,7 +314,7 @@ sv_status sv_init_reference(sv_ctx* c, uint64_t b) {
 }
 
 // Upload a lowered circuit's ops and make sure every circuit-sized buffer fits.
-static sv_status stage_circuit(sv_ctx* c, const HostCircuit& hc) {
+sv_status svqe::stage_circuit(sv_ctx* c, const HostCircuit& hc) {
   const size_t n_ops = hc.ops.size();
   SV_CUDA(grow(c->ops, c->ops_cap, n_ops), c);
   SV_CUDA(grow(c->coef, c->coef_cap, n_ops), c);
@@ -351,8 +351,8 @@ static sv_status forward(sv_ctx* c, const HostCircuit& hc, const double* theta_d
 
 // psi = |ref>, forward, lambda = H psi, adjoint sweep; energy -> energy_dev[0], gradient ->
 // grad_dev.  Everything stream-ordered on c->stream.
-static sv_status adjoint_core(sv_ctx* c, const HostCircuit& hc, const sv_ham* H,
-                              const double* theta_dev, double* energy_dev, double* grad_dev) {
+sv_status svqe::adjoint_core(sv_ctx* c, const HostCircuit& hc, const sv_ham* H,
+                       const double* theta_dev, double* energy_dev, double* grad_dev) {
   SV_CUDA(launch_init_basis(c->psi, c->n, c->ref, c->stream), c);
   sv_status st = forward(c, hc, theta_dev);
   if (st != SV_OK) return st;
@@ -443,6 +443,30 @@ sv_status sv_adjoint_grad(sv_ctx* c, const sv_circuit* circ, const double* theta
   return SV_OK;
 }
 
+sv_status svqe::vqe_enqueue(sv_ctx* c, const HostCircuit& hc, const sv_ham* H, const double* theta_in,
+                      double lr, int32_t n_steps, double* theta_out, double* energy_out) {
+  sv_status st = stage_circuit(c, hc);
+  if (st != SV_OK) return st;
+  SV_CUDA(grow(c->etraj, c->etraj_cap, (size_t)std::max(1, n_steps)), c);
+  if (hc.n_params)
+    SV_CUDA(cudaMemcpyAsync(c->theta, theta_in, hc.n_params * sizeof(double),
+                            cudaMemcpyHostToDevice, c->stream), c);
+  for (int t = 0; t < n_steps; ++t) {
+    if ((st = adjoint_core(c, hc, H, c->theta, c->scal, c->grad)) != SV_OK) return st;
+    SV_CUDA(launch_gd_update(c->theta, c->grad, hc.n_params, lr, c->scal, c->etraj + t,
+                             c->stream), c);
+  }
+  if (hc.n_params)
+    SV_CUDA(cudaMemcpyAsync(theta_out, c->theta, hc.n_params * sizeof(double),
+                            cudaMemcpyDeviceToHost, c->stream), c);
+  if (energy_out && n_steps > 0)
+    SV_CUDA(cudaMemcpyAsync(energy_out, c->etraj, n_steps * sizeof(double),
+                            cudaMemcpyDeviceToHost, c->stream), c);
+  return SV_OK;
+}
+
+cudaStream_t svqe::ctx_stream(sv_ctx* c) { return c->stream; }
+
 sv_status vqe_step(sv_ctx* c, const sv_circuit* circ, const sv_ham* H, double* theta_inout,
                    double lr, int32_t n_steps, double* energy_out) {
   clear_error();
@@ -454,22 +478,8 @@ sv_status vqe_step(sv_ctx* c, const sv_circuit* circ, const sv_ham* H, double* t
   sv_status st = lower_circuit(circ, c->n, hc);
   if (st != SV_OK) return st;
   if (hc.n_params > 0 && !theta_inout) { set_error("theta is NULL"); return SV_EINVAL; }
-  if ((st = stage_circuit(c, hc)) != SV_OK) return st;
-  SV_CUDA(grow(c->etraj, c->etraj_cap, (size_t)std::max(1, n_steps)), c);
-  if (hc.n_params)
-    SV_CUDA(cudaMemcpyAsync(c->theta, theta_inout, hc.n_params * sizeof(double),
-                            cudaMemcpyHostToDevice, c->stream), c);
-  for (int t = 0; t < n_steps; ++t) {
-    if ((st = adjoint_core(c, hc, H, c->theta, c->scal, c->grad)) != SV_OK) return st;
-    SV_CUDA(launch_gd_update(c->theta, c->grad, hc.n_params, lr, c->scal, c->etraj + t,
-                             c->stream), c);
-  }
-  if (hc.n_params)
-    SV_CUDA(cudaMemcpyAsync(theta_inout, c->theta, hc.n_params * sizeof(double),
-                            cudaMemcpyDeviceToHost, c->stream), c);
-  if (energy_out && n_steps > 0)
-    SV_CUDA(cudaMemcpyAsync(energy_out, c->etraj, n_steps * sizeof(double),
-                            cudaMemcpyDeviceToHost, c->stream), c);
+  if ((st = vqe_enqueue(c, hc, H, theta_inout, lr, n_steps, theta_inout, energy_out)) != SV_OK)
+    return st;
   SV_CUDA(cudaStreamSynchronize(c->stream), c);
   return SV_OK;
 }
@@ -503,13 +513,62 @@ sv_status sv_state_device_ptr(sv_ctx* c, void** psi_dev) {
 // ------------------------------------------------------------------------------ batches
 static constexpr int kTableBitsBatch = SV_BATCH_MAX_QUBITS;  // full diagonal tables allowed
 
+// Team class of an instance: 0 (8 warps, n <= 12), 1 (4 warps, n <= 11), 2 (1 warp, n <= 9).
+int svqe::batch_class(int n) { return n <= kClassQubits[2] ? 2 : n <= kClassQubits[1] ? 1 : 0; }
+int svqe::class_teams(int n) {
+  const int c = batch_class(n);
+  return c == 0 ? 1 : c == 1 ? 2 : 8;
+}
+
+// Work items: instances sorted by cost (largest first), class-0 instances alone, class-1
+// instances in pairs and class-2 instances in groups of eight of similar cost; items sorted by
+// the cost of their first (largest) instance.
+std::vector<BItem> svqe::batch_items(const std::vector<BInst>& bi, const std::vector<double>& cost) {
+  const int n = (int)bi.size();
+  std::vector<int> order(n);
+  std::iota(order.begin(), order.end(), 0);
+  std::stable_sort(order.begin(), order.end(), [&](int a, int c) { return cost[a] > cost[c]; });
+  std::vector<BItem> items;
+  std::vector<double> icost;
+  BItem open[3];
+  int fill[3] = {0, 0, 0};
+  const int cap[3] = {1, 2, 8};
+  for (int c = 0; c < 3; ++c) {
+    open[c].cls = c;
+    for (int t = 0; t < 8; ++t) open[c].inst[t] = -1;
+  }
+  std::vector<double> first_cost(3, 0.0);
+  for (int i : order) {
+    const int c = batch_class(bi[i].n);
+    if (fill[c] == 0) first_cost[c] = cost[i];
+    open[c].inst[fill[c]++] = i;
+    if (fill[c] == cap[c]) {
+      items.push_back(open[c]);
+      icost.push_back(first_cost[c]);
+      fill[c] = 0;
+      for (int t = 0; t < 8; ++t) open[c].inst[t] = -1;
+    }
+  }
+  for (int c = 0; c < 3; ++c)
+    if (fill[c] > 0) {
+      items.push_back(open[c]);
+      icost.push_back(first_cost[c]);
+    }
+  std::vector<int> io(items.size());
+  std::iota(io.begin(), io.end(), 0);
+  std::stable_sort(io.begin(), io.end(), [&](int a, int c) { return icost[a] > icost[c]; });
+  std::vector<BItem> out;
+  for (int k : io) out.push_back(items[k]);
+  return out;
+}
+
 // FP64 flops (FMA = 2) of one instance's forward pass, lambda = H psi and adjoint sweep, as
 // k_batch executes its segments: lifting rotation 12 per pair, gradient 8 per pair, H gate 8
 // per pair; a diagonal segment 12 per amplitude forward and 16 + (RZ gates on bits >= 8)
 // backward; a commuting layer un-applies lambda only; groups 4 (real or imaginary table) or 8
 // (complex) per amplitude plus 4 for the energy.
-static double batch_instance_flops(const HostCircuit& hc, const HostHam& hh,
-                                   const std::vector<Seg>& segs) {
+double svqe::batch_instance_flops(const HostCircuit& hc, const HostHam& hh,
+                            const std::vector<Seg>& segs) {
   const double N = (double)(1u << hc.n);
   double f = 0.0;
   for (const Seg& s : segs) {
@@ -531,7 +590,7 @@ static double batch_instance_flops(const HostCircuit& hc, const HostHam& hh,
       f += N * (12 + 16 + hi);
     }
   }
-  for (const DGroup& g : hh.groups) f += N * (g.cls == 2 ? 8 : 4);
+  for (const DGroup& g : hh.groups) f += N * ((g.cls & 3) == 2 ? 8 : 4);
   f += N * 4;
   return f;
 }
@@ -542,7 +601,7 @@ sv_status sv_batch_free(sv_batch* b) {
   if (b->stream) cudaStreamSynchronize(b->stream);
   if (b->exec) cudaGraphExecDestroy(b->exec);
   cudaFree(b->inst);
-  cudaFree(b->order);
+  cudaFree(b->items);
   cudaFree(b->ops);
   cudaFree(b->groups);
   cudaFree(b->tables);
@@ -591,12 +650,14 @@ sv_status sv_batch_create(const sv_instance* inst, int32_t n, void* stream, sv_b
     if (I.ref >= (1ull << hc.n)) { set_error("instance %d: reference index out of range", i); return SV_EINVAL; }
     std::vector<Seg> sg;
     const int n_ckpt = segment_ops(hc.ops, 2, 3, sg);
-    flops += batch_instance_flops(hc, hh, sg);
+    const double inst_flops = batch_instance_flops(hc, hh, sg);
+    flops += inst_flops;
     bytes += (double)hc.ops.size() * (sizeof(DOp) + sizeof(Rot) * 2 + 2 * sizeof(double)) +
              (double)hh.groups.size() * sizeof(DGroup) +
              (double)hh.tables.size() * sizeof(double2) + 3.0 * 8 * hc.n_params + 8 +
              2.0 * n_ckpt * sizeof(double2) * (double)(1u << hc.n);
     BInst& B = bi[i];
+    B = BInst{};
     B.n = hc.n;
     B.n_ops = (int)hc.ops.size();
     B.n_groups = (int)hh.groups.size();
@@ -605,12 +666,15 @@ sv_status sv_batch_create(const sv_instance* inst, int32_t n, void* stream, sv_b
     B.n_ckpt = n_ckpt;
     B.ref = I.ref;
     B.op_off = (int64_t)ops.size();
+    B.coef_off = B.op_off;
+    B.contrib_off = B.op_off;
     B.grp_off = (int64_t)groups.size();
     B.theta_off = theta_off;
     B.seg_off = (int64_t)segs.size();
     B.pp_off = (int64_t)pptr.size();
     theta_off += hc.n_params;
-    ckpt_slot = std::max<int64_t>(ckpt_slot, (int64_t)n_ckpt << hc.n);
+    // a CTA's checkpoint region is split evenly among the teams of the instance's class
+    ckpt_slot = std::max<int64_t>(ckpt_slot, ((int64_t)n_ckpt << hc.n) * class_teams(hc.n));
     segs.insert(segs.end(), sg.begin(), sg.end());
     // parameter -> ops using it, in op order (CSR)
     std::vector<std::vector<int32_t>> uses(hc.n_params);
@@ -629,7 +693,7 @@ sv_status sv_batch_create(const sv_instance* inst, int32_t n, void* stream, sv_b
     tables.insert(tables.end(), hh.tables.begin(), hh.tables.end());
     ops.insert(ops.end(), hc.ops.begin(), hc.ops.end());
     nmax = std::max(nmax, hc.n);
-    cost[i] = (double)(1u << hc.n) * (3.0 * B.n_ops + 1.0 * B.n_groups + 8.0);
+    cost[i] = inst_flops + 64.0 * B.n_ops + 1.0;  // per-op latency matters for tiny states
   }
   sv_batch* b = new (std::nothrow) sv_batch();
   if (!b) { set_error("host allocation failed"); return SV_ENOMEM; }
@@ -647,14 +711,14 @@ sv_status sv_batch_create(const sv_instance* inst, int32_t n, void* stream, sv_b
     if (e != cudaSuccess) { set_error("cudaStreamCreate: %s", cudaGetErrorString(e)); delete b; return SV_ECUDA; }
     b->own_stream = true;
   }
-  std::vector<int32_t> order(n);
-  std::iota(order.begin(), order.end(), 0);
-  std::stable_sort(order.begin(), order.end(), [&](int a, int c) { return cost[a] > cost[c]; });
+  const std::vector<BItem> items = batch_items(bi, cost);
+  b->n_items = (int)items.size();
   auto alloc = [&](void** p, size_t bytes) {
     return cudaMalloc(p, std::max<size_t>(bytes, 16)) == cudaSuccess;
   };
   const size_t P = (size_t)std::max<int64_t>(theta_off, 1);
-  if (!alloc((void**)&b->inst, n * sizeof(BInst)) || !alloc((void**)&b->order, n * sizeof(int32_t)) ||
+  if (!alloc((void**)&b->inst, n * sizeof(BInst)) ||
+      !alloc((void**)&b->items, items.size() * sizeof(BItem)) ||
       !alloc((void**)&b->ops, ops.size() * sizeof(DOp)) ||
       !alloc((void**)&b->groups, groups.size() * sizeof(DGroup)) ||
       !alloc((void**)&b->tables, tables.size() * sizeof(double2)) ||
@@ -676,7 +740,7 @@ sv_status sv_batch_create(const sv_instance* inst, int32_t n, void* stream, sv_b
   };
   cudaError_t e = cudaSuccess;
   if ((e = up(b->inst, bi.data(), n * sizeof(BInst))) != cudaSuccess ||
-      (e = up(b->order, order.data(), n * sizeof(int32_t))) != cudaSuccess ||
+      (e = up(b->items, items.data(), items.size() * sizeof(BItem))) != cudaSuccess ||
       (e = up(b->ops, ops.data(), ops.size() * sizeof(DOp))) != cudaSuccess ||
       (e = up(b->groups, groups.data(), groups.size() * sizeof(DGroup))) != cudaSuccess ||
       (e = up(b->tables, tables.data(), tables.size() * sizeof(double2))) != cudaSuccess ||
@@ -689,7 +753,7 @@ sv_status sv_batch_create(const sv_instance* inst, int32_t n, void* stream, sv_b
     sv_batch_free(b);
     return SV_ECUDA;
   }
-  b->grid = std::min(b->grid, n);
+  b->grid = std::min(b->grid, b->n_items);
   b->smem = batch_smem_bytes(nmax);
   b->ckpt_slot = ckpt_slot;
   if (!alloc((void**)&b->ckpt, (size_t)b->grid * ckpt_slot * sizeof(double2))) {
@@ -721,7 +785,9 @@ static BatchArgs batch_args(sv_batch* b, double* theta, double* energy, double* 
                             int n_steps, double lr, double* etraj) {
   BatchArgs a;
   a.inst = b->inst;
-  a.order = b->order;
+  a.items = b->items;
+  a.n_items = b->n_items;
+  a.smem_amps = kBatchSmemAmps;
   a.n_inst = b->n_inst;
   a.ops = b->ops;
   a.groups = b->groups;
@@ -801,4 +867,3 @@ sv_status sv_batch_vqe_dev(sv_batch* b, double* theta_dev, double lr, int32_t n_
   return SV_OK;
 }
 
-}  // extern "C"

@@ -1,0 +1,34 @@
+// api_internal.h -- library-internal entry points shared by api.cu and serve.cu.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <vector>
+
+#include "../../include/svqe.h"
+#include "host_compile.h"
+#include "launch.h"
+
+namespace svqe {
+
+// Stage a lowered circuit on a context (ops, coefficient and gradient buffers, fused plan).
+sv_status stage_circuit(sv_ctx* c, const HostCircuit& hc);
+// psi = |ref>, forward, lambda = H psi, adjoint sweep; stream-ordered.
+sv_status adjoint_core(sv_ctx* c, const HostCircuit& hc, const sv_ham* H,
+                       const double* theta_dev, double* energy_dev, double* grad_dev);
+// n_steps of gradient descent, enqueued on the context's stream without synchronising:
+// theta_in is read before the call returns; theta_out (n_params) and energy_out (n_steps)
+// are written when the stream reaches them (pinned host memory for real asynchrony).
+sv_status vqe_enqueue(sv_ctx* c, const HostCircuit& hc, const sv_ham* H, const double* theta_in,
+                      double lr, int32_t n_steps, double* theta_out, double* energy_out);
+cudaStream_t ctx_stream(sv_ctx* c);
+
+// Batched-kernel helpers: team class of an n-qubit instance, teams per CTA of that class,
+// work items from per-instance costs, and the FP64 flop count of one instance.
+int batch_class(int n);
+int class_teams(int n);
+std::vector<BItem> batch_items(const std::vector<BInst>& bi, const std::vector<double>& cost);
+double batch_instance_flops(const HostCircuit& hc, const HostHam& hh,
+                            const std::vector<Seg>& segs);
+
+}  // namespace svqe

@@ -384,7 +384,14 @@ sv_status lower_ham(const sv_paulisum* h, int expect_n, int kmax, HostHam& out) 
             im[j] = c2 + d; im[j + len] = c2 - d;
           }
       g.cls = (any_re && any_im) ? 2 : (any_im ? 1 : 0);
-      for (size_t j = 0; j < sz; ++j) out.tables.push_back(make_double2(re[j], im[j]));
+      if (members[u].size() == 1) {
+        // One term: f(k) = coefficient * (-1)^{popc(z & k)}, no table walk (cls 4 real,
+        // 5 imaginary); the single table entry is the coefficient (the transform's entry 0).
+        g.cls += 4;
+        out.tables.push_back(make_double2(re[0], im[0]));
+      } else {
+        for (size_t j = 0; j < sz; ++j) out.tables.push_back(make_double2(re[j], im[j]));
+      }
       out.groups.push_back(g);
     }
     s = e;

@@ -1,10 +1,13 @@
 // k_batch.cu -- the persistent batched kernel: many small independent instances (Sec. 4.1,
 // Eq. 7: every bond length / parameter set is its own problem) in one launch.
 //
-// One CTA runs one instance at a time, taken from a cost-sorted queue with an atomic counter
-// (largest first, so the tail is made of cheap instances).  The instance's psi and lambda
-// (2 x 2^n x 16 bytes, n <= 12) live in shared memory for the forward pass, lambda = H psi
-// and the adjoint sweep.  GB300's FP64 pipe (2 DFMA/clk/SM) is the binding resource, so the
+// A CTA (8 warps) takes work items from a cost-sorted queue with an atomic counter (largest
+// first, so the tail is made of cheap items).  An item is one 12-qubit instance run by all 8
+// warps, two instances of 10-11 qubits run by 4 warps each, or eight instances of at most 9
+// qubits run by one warp each: every instance gets at most 16 amplitudes per thread, and small
+// instances synchronise with __syncwarp or a named barrier instead of the whole CTA.  An
+// instance's psi and lambda (2 x 2^n x 16 bytes) live in its team's share of shared memory for
+// the forward pass, lambda = H psi and the adjoint sweep.  GB300's FP64 pipe (2 DFMA/clk/SM) is the binding resource, so the
 // op list is executed in segments (see Seg) that cut FP64 work:
 //   * a run of RZ/CZ is one diagonal phase per amplitude from two half tables (8 FP64 ops per
 //     amplitude instead of 3 per RZ gate);
@@ -23,30 +26,66 @@ namespace {
 
 constexpr unsigned kFull = 0xffffffffu;
 constexpr int kM = 16;  // values reduced at once (kMaxLayer)
+constexpr int kWarps = kBatchThreads / 32;
 
-template <int BT>
-struct Smem {
-  double red[BT / 32];
-  double red16[BT / 32][kM];
+// Per-team scratch in static shared memory.
+struct TeamS {
+  double red[kWarps];
+  double red16[kWarps][kM];
   double2 tl[64];
   double2 th[64];
   double2 cs[kM];
   int rz_op[kM];
   int rz_bit[kM];
-  int item;
 };
 
-// Sum over the block of one value per thread; result valid in thread 0.  Caller syncs
-// before `red` is reused.
-template <int BT>
-__device__ __forceinline__ double block_sum(double v, double* red) {
+// A team of nw warps running one instance.  Teams of one warp synchronise with __syncwarp,
+// larger teams with named barrier `bar` (barrier 0 is the CTA-wide one).
+struct Team {
+  int nw, size, log_size, rank, w, bar;
+  __device__ __forceinline__ void sync() const {
+    if (nw == 1) {
+      __syncwarp();
+    } else {
+      asm volatile("bar.sync %0, %1;" ::"r"(bar), "r"(size) : "memory");
+    }
+  }
+};
+
+__device__ __forceinline__ uint32_t insert_zeros32(uint32_t p, const uint8_t* sb, int k) {
+#pragma unroll
+  for (int t = 0; t < 4; ++t) {
+    if (t < k) {
+      const uint32_t low = p & ((1u << sb[t]) - 1u);
+      p = ((p >> sb[t]) << (sb[t] + 1)) | low;
+    }
+  }
+  return p;
+}
+
+__device__ __forceinline__ uint32_t pext32(uint32_t i, uint32_t m) {
+  uint32_t r = 0;
+  int k = 0;
+  while (m) {
+    const int pos = __ffs(m) - 1;
+    r |= ((i >> pos) & 1u) << k;
+    ++k;
+    m &= m - 1;
+  }
+  return r;
+}
+
+// Team sum of one value per thread; valid in team rank 0 (every lane of a one-warp team).
+// The caller synchronises the team before S.red is reused.
+__device__ __forceinline__ double team_sum(const Team& T, TeamS& S, double v) {
   v = warp_sum(v);
-  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
-  if (l == 0) red[w] = v;
-  __syncthreads();
+  if (T.nw == 1) return v;
+  if ((threadIdx.x & 31) == 0) S.red[T.w] = v;
+  T.sync();
   double t = 0.0;
-  if (w == 0) {
-    t = (l < BT / 32) ? red[l] : 0.0;
+  if (T.w == 0) {
+    const int l = threadIdx.x & 31;
+    t = l < T.nw ? S.red[l] : 0.0;
     t = warp_sum(t);
   }
   return t;
@@ -70,20 +109,21 @@ __device__ __forceinline__ double warp_sum16(double (&v)[kM]) {
   return v[0] + __shfl_xor_sync(kFull, v[0], 1);
 }
 
-// Block totals of v[0..m): thread j < m returns the total of value j (fixed order); other
-// threads return 0.  Ends synchronised.
-template <int BT>
-__device__ __forceinline__ double block_sum16(double (&v)[kM], int m, double (*red16)[kM]) {
+// Team totals of v[0..m): team rank j < m returns the total of value j, others 0.  Ends with
+// the team synchronised.
+__device__ __forceinline__ double team_sum16(const Team& T, TeamS& S, double (&v)[kM], int m) {
   const double t = warp_sum16(v);
-  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
-  if ((l & 1) == 0) red16[w][l >> 1] = t;
-  __syncthreads();
-  double s = 0.0;
-  if (threadIdx.x < m) {
-#pragma unroll
-    for (int k = 0; k < BT / 32; ++k) s += red16[k][threadIdx.x];
+  const int lane = threadIdx.x & 31;
+  if (T.nw == 1) {
+    const double r = __shfl_sync(kFull, t, (2 * lane) & 31);
+    return lane < m ? r : 0.0;
   }
-  __syncthreads();
+  if ((lane & 1) == 0) S.red16[T.w][lane >> 1] = t;
+  T.sync();
+  double s = 0.0;
+  if (T.rank < m)
+    for (int k = 0; k < T.nw; ++k) s += S.red16[k][T.rank];
+  T.sync();
   return s;
 }
 
@@ -116,50 +156,66 @@ __device__ __forceinline__ double2 cmul_conj(const double2& a, const double2& b)
   return make_double2(fma(a.x, b.x, a.y * b.y), fma(a.y, b.x, dneg(a.x) * b.y));
 }
 
-// Apply one pair op to buffer v (forward or inverse), pairs strided over the block.
-template <int BT>
-__device__ __forceinline__ void op_pass(double2* v, uint32_t N, const DOp& op, const Rot& r,
-                                        bool inv) {
+// Apply one pair op to buffer v (forward or inverse), pairs strided over the team, two pairs
+// per iteration (both loaded before either is stored, so their chains overlap).
+__device__ __forceinline__ void op_pass(const Team& T, double2* v, uint32_t N, const DOp& op,
+                                        const Rot& r, bool inv) {
   const uint32_t np = N >> op.k;
-  for (uint32_t p = threadIdx.x; p < np; p += BT) {
-    const uint32_t i = (uint32_t)insert_zeros(p, op.sb, op.k) | (uint32_t)op.lo_or;
-    if (op.type == SV_GATE_CZ) {
+  const uint32_t lo = (uint32_t)op.lo_or;
+  if (op.type == SV_GATE_CZ) {
+    for (uint32_t p = T.rank; p < np; p += T.size) {
+      const uint32_t i = insert_zeros32(p, op.sb, op.k) | lo;
       v[i] = make_double2(dneg(v[i].x), dneg(v[i].y));
-    } else {
-      const uint32_t j = i ^ (uint32_t)op.flip;
-      double2 x = v[i], y = v[j];
-      pair_apply(op.type, r, inv, x, y);
-      v[i] = x;
-      v[j] = y;
+    }
+    return;
+  }
+  const uint32_t fl = (uint32_t)op.flip;
+  for (uint32_t p = T.rank; p < np; p += 2 * T.size) {
+    const uint32_t p2 = p + T.size;
+    const uint32_t i = insert_zeros32(p, op.sb, op.k) | lo;
+    const uint32_t i2 = insert_zeros32(p2, op.sb, op.k) | lo;
+    double2 x = v[i], y = v[i ^ fl];
+    double2 x2, y2;
+    const bool two = p2 < np;
+    if (two) {
+      x2 = v[i2];
+      y2 = v[i2 ^ fl];
+    }
+    pair_apply(op.type, r, inv, x, y);
+    if (two) pair_apply(op.type, r, inv, x2, y2);
+    v[i] = x;
+    v[i ^ fl] = y;
+    if (two) {
+      v[i2] = x2;
+      v[i2 ^ fl] = y2;
     }
   }
 }
 
 // Build the diagonal segment's half tables: th[hi] * tl[lo] = prod_RZ e^{-i phi s(k)}.
-template <int BT>
-__device__ __forceinline__ int diag_setup(Smem<BT>& S, const DOp* ops, const Seg& sg,
-                                          const double* theta, int n) {
+__device__ __forceinline__ int diag_setup(const Team& T, TeamS& S, const DOp* ops,
+                                          const Seg& sg, const double* theta, int n) {
   int m = 0;
   for (int l = 0; l < sg.count; ++l)
     if (ops[sg.first + l].type == SV_GATE_RZ) {
-      if (threadIdx.x == 0) {
+      if (T.rank == 0) {
         S.rz_op[m] = sg.first + l;
         S.rz_bit[m] = ops[sg.first + l].bit0;
       }
       ++m;
     }
-  __syncthreads();
-  if (threadIdx.x < m) {
-    const DOp op = ops[S.rz_op[threadIdx.x]];
+  T.sync();
+  if (T.rank < m) {
+    const DOp op = ops[S.rz_op[T.rank]];
     const double t = op.param >= 0 ? theta[op.param] : op.fixed;
     double sn, cs;
     sincos(0.5 * t, &sn, &cs);
-    S.cs[threadIdx.x] = make_double2(cs, sn);
+    S.cs[T.rank] = make_double2(cs, sn);
   }
-  __syncthreads();
+  T.sync();
   const int hl = n < 6 ? n : 6;
   const int nl = 1 << hl, nh = 1 << (n - hl);
-  for (int j = threadIdx.x; j < nl + nh; j += BT) {
+  for (int j = T.rank; j < nl + nh; j += T.size) {
     const bool hi = j >= nl;
     const int jj = hi ? j - nl : j;
     double2 p = make_double2(1.0, 0.0);
@@ -172,7 +228,7 @@ __device__ __forceinline__ int diag_setup(Smem<BT>& S, const DOp* ops, const Seg
     }
     if (hi) S.th[jj] = p; else S.tl[jj] = p;
   }
-  __syncthreads();
+  T.sync();
   return m;
 }
 
@@ -186,8 +242,8 @@ __device__ __forceinline__ bool cz_sign(const DOp* ops, const Seg& sg, uint32_t 
   return par & 1u;
 }
 
-template <int BT>
-__device__ void run_instance(const BatchArgs& a, int idx, double2* sm, Smem<BT>& S) {
+__device__ void run_instance(const BatchArgs& a, int idx, const Team& T, TeamS& S, double2* sm,
+                             double2* ck) {
   const BInst I = a.inst[idx];
   const int n = I.n;
   const uint32_t N = 1u << n;
@@ -196,67 +252,99 @@ __device__ void run_instance(const BatchArgs& a, int idx, double2* sm, Smem<BT>&
   const DOp* ops = a.ops + I.op_off;
   const DGroup* groups = a.groups + I.grp_off;
   const Seg* segs = a.segs + I.seg_off;
-  Rot* coef = a.coef + I.op_off;
-  double* contrib = a.contrib + I.op_off;
+  Rot* coef = a.coef + I.coef_off;
+  double* contrib = a.contrib + I.contrib_off;
   double* theta = a.theta + I.theta_off;
   double* grad = a.grad + I.theta_off;
-  double2* ck = a.ckpt + (size_t)blockIdx.x * a.ckpt_slot;
-  const int tid = threadIdx.x;
+  const int tid = T.rank;
+  const int TS = T.size;
   const int hl = n < 6 ? n : 6;
   const uint32_t lmask = (1u << hl) - 1u;
-  const int steps = a.n_steps > 0 ? a.n_steps : 1;
-  const double lr = a.lr_inst ? a.lr_inst[idx] : a.lr;
-  constexpr int kLogBT = BT == 128 ? 7 : BT == 256 ? 8 : BT == 512 ? 9 : 10;
+  const bool per_inst = a.n_steps < 0;
+  const int steps = per_inst ? I.steps : (a.n_steps > 0 ? a.n_steps : 1);
+  const bool gd = a.n_steps != 0;
+  const double lr = per_inst ? I.lr : (a.lr_inst ? a.lr_inst[idx] : a.lr);
 
   for (int step = 0; step < steps; ++step) {
-    for (int g = tid; g < I.n_ops; g += BT) coef[g] = make_coef(ops[g], theta).r;
-    for (uint32_t k = tid; k < N; k += BT)
+    for (int g = tid; g < I.n_ops; g += TS) coef[g] = make_coef(ops[g], theta).r;
+    for (uint32_t k = tid; k < N; k += TS)
       psi[k] = make_double2(k == (uint32_t)I.ref ? 1.0 : 0.0, 0.0);
-    __syncthreads();
+    T.sync();
 
     // ---------------------------------------------------------------- forward
     for (int s = 0; s < I.n_segs; ++s) {
       const Seg sg = segs[s];
       if (sg.ckpt >= 0) {
         double2* dst = ck + (size_t)sg.ckpt * N;
-        for (uint32_t k = tid; k < N; k += BT) dst[k] = psi[k];
-        __syncthreads();
+        for (uint32_t k = tid; k < N; k += TS) dst[k] = psi[k];
+        T.sync();
       }
       if (sg.kind == SEG_DIAG) {
-        diag_setup<BT>(S, ops, sg, theta, n);
-        for (uint32_t k = tid; k < N; k += BT) {
+        diag_setup(T, S, ops, sg, theta, n);
+        for (uint32_t k = tid; k < N; k += TS) {
           const double2 ph = cmul(S.th[k >> hl], S.tl[k & lmask]);
           double2 v = cmul(psi[k], ph);
           if (cz_sign(ops, sg, k)) v = make_double2(dneg(v.x), dneg(v.y));
           psi[k] = v;
         }
-        __syncthreads();
+        T.sync();
       } else {
         for (int l = sg.first; l < sg.first + sg.count; ++l) {
-          op_pass<BT>(psi, N, ops[l], coef[l], false);
-          __syncthreads();
+          op_pass(T, psi, N, ops[l], coef[l], false);
+          T.sync();
         }
       }
     }
 
     // ---------------------------------------------------------------- lambda = H psi
+    // Each thread carries kHU amplitudes through the group loop: kHU independent multiply-add
+    // chains and table loads in flight, one group-record load per kHU amplitudes.
     double e = 0.0;
-    for (uint32_t k = tid; k < N; k += BT) {
-      double2 acc = make_double2(0.0, 0.0);
+    constexpr int kHU = 4;
+    for (uint32_t k0 = tid; k0 < N; k0 += kHU * TS) {
+      double2 acc[kHU];
+#pragma unroll
+      for (int u = 0; u < kHU; ++u) acc[u] = make_double2(0.0, 0.0);
       for (int g = 0; g < I.n_groups; ++g) {
         const DGroup G = groups[g];
-        const double2 v = psi[k ^ (uint32_t)G.x];
-        const uint32_t ti = (G.zu == (uint64_t)(N - 1)) ? k : pext64(k, G.zu);
-        const double2 f = a.tables[G.toff + ti];
-        group_madd(G.cls, f, v, acc);
+        const uint32_t x = (uint32_t)G.x, zu = (uint32_t)G.zu;
+        if (G.cls >= 4) {
+          const double2 c = a.tables[G.toff];
+          const int cls = G.cls - 4;
+#pragma unroll
+          for (int u = 0; u < kHU; ++u) {
+            const uint32_t k = k0 + u * TS;
+            if (k < N) {
+              double2 f = c;
+              if (__popc(k & zu) & 1) f = make_double2(dneg(f.x), dneg(f.y));
+              group_madd(cls, f, psi[k ^ x], acc[u]);
+            }
+          }
+        } else {
+          const bool full = zu == N - 1;
+#pragma unroll
+          for (int u = 0; u < kHU; ++u) {
+            const uint32_t k = k0 + u * TS;
+            if (k < N) {
+              const uint32_t ti = full ? k : pext32(k, zu);
+              group_madd(G.cls, a.tables[G.toff + ti], psi[k ^ x], acc[u]);
+            }
+          }
+        }
       }
-      lam[k] = acc;
-      const double2 p = psi[k];
-      e = fma(p.x, acc.x, e);
-      e = fma(p.y, acc.y, e);
+#pragma unroll
+      for (int u = 0; u < kHU; ++u) {
+        const uint32_t k = k0 + u * TS;
+        if (k < N) {
+          lam[k] = acc[u];
+          const double2 p = psi[k];
+          e = fma(p.x, acc[u].x, e);
+          e = fma(p.y, acc[u].y, e);
+        }
+      }
     }
-    const double E = block_sum<BT>(e, S.red);
-    __syncthreads();
+    const double E = team_sum(T, S, e);
+    T.sync();
 
     // ---------------------------------------------------------------- adjoint sweep
     for (int s = I.n_segs - 1; s >= 0; --s) {
@@ -267,14 +355,15 @@ __device__ void run_instance(const BatchArgs& a, int idx, double2* sm, Smem<BT>&
           const Rot r = coef[l];
           const uint32_t np = N >> op.k;
           const bool pg = op.param >= 0;
+          const uint32_t lo = (uint32_t)op.lo_or, fl = (uint32_t)op.flip;
           double acc = 0.0;
-          for (uint32_t p = tid; p < np; p += BT) {
-            const uint32_t i = (uint32_t)insert_zeros(p, op.sb, op.k) | (uint32_t)op.lo_or;
+          for (uint32_t p = tid; p < np; p += TS) {
+            const uint32_t i = insert_zeros32(p, op.sb, op.k) | lo;
             if (op.type == SV_GATE_CZ) {
               psi[i] = make_double2(dneg(psi[i].x), dneg(psi[i].y));
               lam[i] = make_double2(dneg(lam[i].x), dneg(lam[i].y));
             } else {
-              const uint32_t j = i ^ (uint32_t)op.flip;
+              const uint32_t j = i ^ fl;
               double2 px = psi[i], py = psi[j], lx = lam[i], ly = lam[j];
               if (pg) pair_grad_acc(op.type, lx, ly, px, py, acc);
               pair_apply(op.type, r, true, px, py);
@@ -286,10 +375,10 @@ __device__ void run_instance(const BatchArgs& a, int idx, double2* sm, Smem<BT>&
             }
           }
           if (pg) {
-            const double t = block_sum<BT>(acc, S.red);
+            const double t = team_sum(T, S, acc);
             if (tid == 0) contrib[l] = t;
           }
-          __syncthreads();
+          T.sync();
         }
         continue;
       }
@@ -300,35 +389,41 @@ __device__ void run_instance(const BatchArgs& a, int idx, double2* sm, Smem<BT>&
         // gradients of every gate from (psi, lambda) at the layer's end
         for (int g = 0; g < sg.count; ++g) {
           const DOp op = ops[sg.first + g];
-          double acc = 0.0;
+          const uint32_t fl = (uint32_t)op.flip;
+          double acc = 0.0, acc2 = 0.0;  // two chains: even and odd iterations
           const uint32_t np = N >> 1;
-          for (uint32_t p = tid; p < np; p += BT) {
-            const uint32_t i = (uint32_t)insert_zeros(p, op.sb, 1);
-            const uint32_t j = i ^ (uint32_t)op.flip;
-            pair_grad_acc(op.type, lam[i], lam[j], psi[i], psi[j], acc);
+          for (uint32_t p = tid; p < np; p += 2 * TS) {
+            const uint32_t i = insert_zeros32(p, op.sb, 1);
+            pair_grad_acc(op.type, lam[i], lam[i ^ fl], psi[i], psi[i ^ fl], acc);
+            const uint32_t p2 = p + TS;
+            if (p2 < np) {
+              const uint32_t i2 = insert_zeros32(p2, op.sb, 1);
+              pair_grad_acc(op.type, lam[i2], lam[i2 ^ fl], psi[i2], psi[i2 ^ fl], acc2);
+            }
           }
+          acc += acc2;
 #pragma unroll
           for (int q = 0; q < kM; ++q)
             if (q == g) v[q] = acc;
         }
-        const double tot = block_sum16<BT>(v, sg.count, S.red16);
+        const double tot = team_sum16(T, S, v, sg.count);
         if (tid < sg.count) contrib[sg.first + tid] = tot;
         // un-apply the layer to lambda
         for (int l = sg.first + sg.count - 1; l >= sg.first; --l) {
-          op_pass<BT>(lam, N, ops[l], coef[l], true);
-          __syncthreads();
+          op_pass(T, lam, N, ops[l], coef[l], true);
+          T.sync();
         }
       } else {  // SEG_DIAG
-        const int m = diag_setup<BT>(S, ops, sg, theta, n);
+        const int m = diag_setup(T, S, ops, sg, theta, n);
         double W = 0.0;
-        for (uint32_t k = tid; k < N; k += BT) {
+        for (uint32_t k = tid; k < N; k += TS) {
           const double2 pk = psi[k];
           double2 lk = lam[k];
           const double w = fma(lk.x, pk.y, dneg(lk.y) * pk.x);  // Im(conj(lambda) psi)
           W += w;
 #pragma unroll
           for (int g = 0; g < kM; ++g)
-            if (g < m && S.rz_bit[g] >= kLogBT)
+            if (g < m && S.rz_bit[g] >= T.log_size)
               v[g] += ((k >> S.rz_bit[g]) & 1u) ? dneg(w) : w;
           const double2 ph = cmul(S.th[k >> hl], S.tl[k & lmask]);
           lk = cmul_conj(lk, ph);
@@ -337,62 +432,88 @@ __device__ void run_instance(const BatchArgs& a, int idx, double2* sm, Smem<BT>&
         }
 #pragma unroll
         for (int g = 0; g < kM; ++g)
-          if (g < m && S.rz_bit[g] < kLogBT)
+          if (g < m && S.rz_bit[g] < T.log_size)
             v[g] = (((uint32_t)tid >> S.rz_bit[g]) & 1u) ? dneg(W) : W;
-        const double tot = block_sum16<BT>(v, m, S.red16);
+        const double tot = team_sum16(T, S, v, m);
         if (tid < m) contrib[S.rz_op[tid]] = tot;
       }
       // psi before the segment, from the forward pass's checkpoint
       const double2* src = ck + (size_t)sg.ckpt * N;
-      for (uint32_t k = tid; k < N; k += BT) psi[k] = src[k];
-      __syncthreads();
+      for (uint32_t k = tid; k < N; k += TS) psi[k] = src[k];
+      T.sync();
     }
 
     // ---------------------------------------------------------------- gradients, update
-    for (int p = tid; p < I.n_params; p += BT) {
+    for (int p = tid; p < I.n_params; p += TS) {
       double g = 0.0;
       for (int j = a.pptr[I.pp_off + p]; j < a.pptr[I.pp_off + p + 1]; ++j)
         g += contrib[a.pops[j]];
       grad[p] = g;
-      if (a.n_steps > 0) theta[p] = fma(-lr, g, theta[p]);
+      if (gd) theta[p] = fma(-lr, g, theta[p]);
     }
     if (tid == 0) {
-      if (a.n_steps > 0 && a.etraj) a.etraj[(size_t)step * a.n_inst + idx] = E;
+      if (gd && a.etraj) {
+        if (per_inst) a.etraj[I.etraj_off + step] = E;
+        else a.etraj[(size_t)step * a.n_inst + idx] = E;
+      }
       a.energy[idx] = E;
     }
-    __syncthreads();
+    T.sync();
   }
 }
 
-template <int BT>
-__global__ void __launch_bounds__(BT, 1) k_batch(BatchArgs a) {
+__global__ void __launch_bounds__(kBatchThreads, 1) k_batch(BatchArgs a) {
   extern __shared__ double2 sm[];
-  __shared__ Smem<BT> S;
+  __shared__ TeamS S[kWarps];
+  __shared__ int s_item;
+  const int wi = threadIdx.x >> 5;
   for (;;) {
-    if (threadIdx.x == 0) S.item = atomicAdd(a.counter, 1);
+    if (threadIdx.x == 0) s_item = atomicAdd(a.counter, 1);
     __syncthreads();
-    const int item = S.item;
+    const int item = s_item;
     __syncthreads();
-    if (item >= a.n_inst) break;
-    run_instance<BT>(a, a.order[item], sm, S);
+    if (item >= a.n_items) break;
+    const int cls = a.items[item].cls;
+    // team layout of the item's class: 1 x 8 warps, 2 x 4 warps or 8 x 1 warp
+    const int nw = cls == 0 ? kWarps : cls == 1 ? kWarps / 2 : 1;
+    const int team = wi / nw;
+    Team T;
+    T.nw = nw;
+    T.size = nw * 32;
+    T.log_size = nw == 8 ? 8 : nw == 4 ? 7 : 5;
+    T.rank = threadIdx.x - team * T.size;
+    T.w = wi - team * nw;
+    T.bar = 1 + team;
+    const int inst = a.items[item].inst[team];
+    if (inst >= 0) {
+      const int nteams = kWarps / nw;
+      double2* region = sm + (size_t)team * (a.smem_amps / nteams);
+      double2* ck = a.ckpt + (size_t)blockIdx.x * a.ckpt_slot +
+                    (size_t)team * (a.ckpt_slot / nteams);
+      run_instance(a, inst, T, S[team], region, ck);
+    }
+    __syncthreads();
   }
 }
 
 }  // namespace
 
-size_t batch_smem_bytes(int nmax) { return (size_t)2 * ((size_t)1 << nmax) * sizeof(double2); }
+size_t batch_smem_bytes(int nmax) {
+  (void)nmax;
+  return (size_t)kBatchSmemAmps * sizeof(double2);
+}
 
 cudaError_t batch_prepare(int nmax, int* grid_out) {
   const size_t smem = batch_smem_bytes(nmax);
-  cudaError_t e = cudaFuncSetAttribute(k_batch<kBatchThreads>,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaError_t e = cudaFuncSetAttribute(k_batch, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)smem);
   if (e != cudaSuccess) return e;
   int dev = 0, sms = 0, per_sm = 0;
   if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
   if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess)
     return e;
-  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch<kBatchThreads>,
-                                                         kBatchThreads, smem)) != cudaSuccess)
+  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch, kBatchThreads,
+                                                         smem)) != cudaSuccess)
     return e;
   if (per_sm < 1) return cudaErrorInvalidConfiguration;
   *grid_out = sms * per_sm;
@@ -400,7 +521,7 @@ cudaError_t batch_prepare(int nmax, int* grid_out) {
 }
 
 cudaError_t launch_batch(const BatchArgs& a, int grid, size_t smem, cudaStream_t s) {
-  k_batch<kBatchThreads><<<grid, kBatchThreads, smem, s>>>(a);
+  k_batch<<<grid, kBatchThreads, smem, s>>>(a);
   return cudaGetLastError();
 }
 

@@ -198,8 +198,9 @@ __global__ void __launch_bounds__(kThreads) k_hpsi(const double2* __restrict__ p
           const uint64_t k = k0 + u * stride;
           if (k < N) {
             const double2 v = psi[k ^ G.x];
-            const double2 f = tables[G.toff + pext64(k, G.zu)];
-            group_madd(G.cls, f, v, acc[u]);
+            double2 f;
+            const int cls = group_value(G, k, tables, f);
+            group_madd(cls, f, v, acc[u]);
           }
         }
       }

@@ -51,40 +51,58 @@ cudaError_t launch_bpass(double2* psi, double2* lam, const FPass& P, const FItem
                          const DOp* gops, const Rot* coef, const double* theta, double* partial,
                          cudaStream_t s);
 
-// One instance of a compiled batch (device record).
+// One instance of a compiled batch (device record).  steps, lr and etraj_off are used when
+// BatchArgs::n_steps < 0 (per-instance step counts, as the serving loop runs them).
 struct BInst {
   int32_t n, n_ops, n_groups, n_params, n_segs, n_ckpt;
+  int32_t steps, pad;
   uint64_t ref;
-  int64_t op_off, grp_off, theta_off, seg_off, pp_off;
+  int64_t op_off, grp_off, theta_off, seg_off, pp_off, etraj_off;
+  int64_t coef_off, contrib_off;  // scratch offsets (Rot / double units)
+  double lr;
 };
-static_assert(sizeof(BInst) == 72, "BInst layout");
+static_assert(sizeof(BInst) == 112, "BInst layout");
+
+// A work item of the batched kernel: one instance on the CTA's 8 warps (cls 0, n <= 12), two
+// instances on 4 warps each (cls 1, n <= 11) or eight on one warp each (cls 2, n <= 9); unused
+// entries of inst are -1.
+struct BItem {
+  int32_t cls;
+  int32_t inst[8];
+};
+static_assert(sizeof(BItem) == 36, "BItem layout");
+constexpr int kClassQubits[3] = {12, 11, 9};
 
 struct BatchArgs {
   const BInst* inst;
-  const int32_t* order;    // instance indices, most expensive first
   int n_inst;
+  const BItem* items;      // most expensive first
+  int n_items;
   const DOp* ops;
   const DGroup* groups;
   const double2* tables;
   const Seg* segs;
   const int32_t* pptr;     // per instance n_params+1 offsets into pops (absolute)
   const int32_t* pops;     // op indices (relative to the instance) using each parameter
-  double* theta;           // concatenated parameters (updated in place when n_steps > 0)
+  double* theta;           // concatenated parameters (updated in place when n_steps != 0)
   double* energy;          // [n_inst]
   double* grad;            // concatenated gradients
   Rot* coef;               // scratch, one per op
   double* contrib;         // scratch, one per op
-  double2* ckpt;           // scratch, ckpt_slot amplitudes per CTA
+  double2* ckpt;           // scratch, ckpt_slot amplitudes per CTA, split evenly among teams
   int64_t ckpt_slot;
+  int64_t smem_amps;       // dynamic shared memory per CTA, in amplitudes
   int* counter;            // work-queue head, zeroed before each launch
-  int n_steps;             // 0: one evaluation; > 0: that many gradient-descent updates
-  double lr;               // step when lr_inst == nullptr
+  int n_steps;             // 0: one evaluation; > 0: that many updates; < 0: BInst::steps
+  double lr;               // step when lr_inst == nullptr (n_steps > 0)
   const double* lr_inst;   // per-instance steps, or nullptr
-  double* etraj;           // [n_steps x n_inst] energies before each update, or nullptr
+  double* etraj;           // energies before each update ([n_steps x n_inst], or per
+                           // instance at BInst::etraj_off when n_steps < 0), or nullptr
 };
 
 // Threads per CTA of the batched kernel and its dynamic shared memory for nmax qubits.
 constexpr int kBatchThreads = 256;
+constexpr int64_t kBatchSmemAmps = 2 * 4096;  // psi + lambda of one 12-qubit instance
 size_t batch_smem_bytes(int nmax);
 cudaError_t batch_prepare(int nmax, int* grid_out);
 cudaError_t launch_batch(const BatchArgs& a, int grid, size_t smem, cudaStream_t s);

@@ -204,6 +204,18 @@ __device__ __forceinline__ void group_madd(int cls, const double2& f, const doub
   }
 }
 
+// f_g(k) of a group (see DGroup); returns the class of the value (0 real, 1 imag, 2 complex).
+__device__ __forceinline__ int group_value(const DGroup& G, uint64_t k, const double2* tables,
+                                           double2& f) {
+  if (G.cls >= 4) {
+    f = tables[G.toff];
+    if (__popcll(k & G.zu) & 1) f = make_double2(dneg(f.x), dneg(f.y));
+    return G.cls - 4;
+  }
+  f = tables[G.toff + pext64(k, G.zu)];
+  return G.cls;
+}
+
 // ------------------------------------------------------------------------------ reductions
 __device__ __forceinline__ double warp_sum(double v) {
 #pragma unroll

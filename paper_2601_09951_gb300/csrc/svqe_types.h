@@ -35,8 +35,11 @@ struct Rot {
 };
 static_assert(sizeof(Rot) == 24, "Rot layout");
 
-// An X-mask group of Pauli terms: f(i) = table[pext(i, zu)], cls says whether the table is
-// real (0), purely imaginary (1) or complex (2).
+// An X-mask group of Pauli terms, (H psi)[k] += f(k) psi[k ^ x]:
+//   cls 0/1/2: f(k) = table[toff + pext(k, zu)], a real / imaginary / complex table over the
+//              kz bits of the union zu of the group's z masks;
+//   cls 4/5:   a single term, f(k) = table[toff] * (-1)^{popc(zu & k)} with zu its z mask and
+//              table[toff] real (4) or imaginary (5).
 struct DGroup {
   uint64_t x;
   uint64_t zu;
