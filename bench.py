@@ -39,6 +39,10 @@ def parse():
     ap.add_argument("--seed", type=int, default=1002)
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", default="batch", choices=["batch", "serve"],
+                    help="batch: the batched evaluation step (default); serve: the request "
+                         "loop (latency percentiles), printed as its own JSON line")
+    ap.add_argument("--requests", type=int, default=300)
     return ap.parse_args()
 
 
@@ -164,11 +168,73 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def run_serve(args):
+    """Serving stream: Poisson arrivals of VQE requests (n log-uniform in 4..24, 20 gradient
+    steps each).  Saturated throughput first (all requests at once), then arrivals at 25, 50,
+    75 and 90 % of it with p50/p99 latency, beside the same stream through the serial
+    one-request-at-a-time server."""
+    import threading
+    import torch
+    torch.cuda.set_device(0)
+    from paper_2601_09951_gb300 import build as libbuild
+    libbuild.build()
+    from paper_2601_09951_gb300 import svqe
+    from paper_2601_09951_gb300 import workloads as W
+    reqs = W.serve_stream(args.requests, 1.0, seed=1005)
+
+    def run(rate, serial=False, budget=64 << 30):
+        srv = svqe.Server(hbm_budget_bytes=budget, steps_per_tick=2, serial=serial)
+        ids = [None] * len(reqs)
+        t0 = time.perf_counter()
+
+        def submitter():
+            for k, r in enumerate(reqs):
+                if rate:
+                    delay = r["arrival_s"] / rate * 1.0 - (time.perf_counter() - t0)
+                    if delay > 0:
+                        time.sleep(delay)
+                ids[k] = srv.submit(r, r["steps"], r["lr"])
+
+        th = threading.Thread(target=submitter)
+        th.start()
+        th.join()
+        lat = []
+        for rid in ids:
+            _, _, info = srv.wait(rid, -1)
+            lat.append(info.done_s - info.submit_s)
+        wall = time.perf_counter() - t0
+        st = srv.stats()
+        srv.close()
+        evals = sum(r["steps"] for r in reqs)
+        return {"evals_per_s": evals / wall, "p50_ms": 1e3 * float(np.percentile(lat, 50)),
+                "p99_ms": 1e3 * float(np.percentile(lat, 99)), "wall_s": wall,
+                "launches": int(st.launches), "peak_bytes": int(st.peak_bytes_in_use)}
+
+    sat = run(None)
+    req_rate = args.requests / sat["wall_s"]  # requests/s at saturation
+    sweep = {}
+    for frac in (0.25, 0.5, 0.75, 0.9):
+        # arrival_s in the stream is for 1 request/s; scale to frac of saturation
+        sweep[f"{int(frac * 100)}%"] = run(frac * req_rate)
+    serial_sat = run(None, serial=True)
+    serial_at_50 = run(0.5 * req_rate, serial=True)
+    line = {"metric": "serving: VQE energy+grad evals/s and p50/p99 request latency",
+            "workload": f"serve_stream_{args.requests}_n4-24_20steps", "unit": "evals/s",
+            "value": sat["evals_per_s"], "saturated": sat, "poisson": sweep,
+            "serial_saturated": serial_sat, "serial_at_50%": serial_at_50,
+            "data": "synthetic (seeded Poisson stream)", "dtype": "f64"}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     rank, world, local = dist_env()
     if args.impl == "reference":
         run_reference(args)
+        return
+    if args.workload == "serve":
+        if rank == 0:
+            run_serve(args)
         return
     import torch
     torch.cuda.set_device(local)

@@ -217,6 +217,70 @@ sv_status sv_batch_run_dev(sv_batch* b, const double* theta_dev, double* energy_
 sv_status sv_batch_vqe_dev(sv_batch* b, double* theta_dev, double lr, int32_t n_steps,
                            double* energy_traj_dev);
 
+/* ---------------------------------------------------------------- serving */
+
+/* A request loop that serves many independent VQE optimisations (Sec. 4.1, Eq. 7: every
+ * problem is independent) as they arrive.  A scheduler thread admits queued requests in
+ * arrival order while their device footprint fits hbm_budget_bytes.  Requests of at most
+ * SV_BATCH_MAX_QUBITS qubits become resident in a device arena (program, tables, parameters,
+ * trajectory) and advance together, steps_per_tick gradient steps per persistent batched
+ * launch; a request that arrives while a launch runs joins at the next launch, and one that
+ * finishes leaves and frees its memory.  Larger requests get their own state buffers and
+ * stream and run concurrently with the batched launches (at most max_active_large at once).
+ * Each request runs n_steps of gradient descent theta <- theta - lr * dE/dtheta from theta0
+ * (Algorithm 1's loop with a fixed step) and returns its final theta and the energies before
+ * each update.  A request's results do not depend on which other requests shared its launches.
+ * serial = 1 runs one request at a time, with no batching (the one-circuit-at-a-time baseline).
+ * Zero fields take defaults: 4 GiB, 4096, 1, 4.  The server reserves a device arena of
+ * min(hbm_budget_bytes, 6 GiB) for small requests at creation; large requests allocate their
+ * own buffers when admitted.  The admitted requests' footprints never sum above the budget. */
+typedef struct {
+  uint64_t hbm_budget_bytes;
+  int32_t max_active_small;
+  int32_t steps_per_tick;
+  int32_t max_active_large;
+  int32_t serial;
+} sv_server_config;
+
+/* Times are seconds since the server was created. */
+typedef struct {
+  uint64_t id;
+  int32_t status;      /* SV_OK done; SV_EBUSY queued or running; otherwise the failure */
+  int32_t n_qubits;
+  int32_t n_params;
+  int32_t n_steps;
+  uint64_t footprint_bytes;
+  double submit_s;
+  double admit_s;
+  double done_s;
+} sv_request_info;
+
+typedef struct {
+  uint64_t submitted, completed, failed, cancelled;
+  uint64_t launches;           /* batched launches issued */
+  uint64_t bytes_in_use;       /* device bytes held by admitted requests now */
+  uint64_t peak_bytes_in_use;  /* never above hbm_budget_bytes */
+  int32_t queued, running;
+} sv_server_stats;
+
+/* Create a server on the current device (allocates its arena and scratch). */
+sv_status sv_server_create(const sv_server_config* cfg, sv_server** out);
+/* Queue a request.  The instance and theta0 (circuit.n_params angles) are copied; validation
+ * errors and a footprint larger than the whole budget are returned here (SV_EINVAL /
+ * SV_ENOMEM).  *id receives the request's id. */
+sv_status sv_server_submit(sv_server* s, const sv_instance* inst, const double* theta0,
+                           int32_t n_steps, double lr, uint64_t* id);
+/* Wait up to timeout_ms (< 0: forever) for request id.  SV_ETIMEOUT if it has not finished;
+ * otherwise its final status, with theta_out (n_params) and energy_out (n_steps) filled when
+ * not NULL and info when not NULL.  A finished request is forgotten after this call. */
+sv_status sv_server_wait(sv_server* s, uint64_t id, int32_t timeout_ms, double* theta_out,
+                         double* energy_out, sv_request_info* info);
+/* Cancel a request that is still queued (SV_EBUSY if it is already running). */
+sv_status sv_server_cancel(sv_server* s, uint64_t id);
+sv_status sv_server_get_stats(sv_server* s, sv_server_stats* out);
+/* Cancel queued requests, finish running ones, free everything. */
+sv_status sv_server_destroy(sv_server* s);
+
 /* ---------------------------------------------------------------- no device allocation */
 
 /* This entry point has no counterpart in the paper; it exists for callers that cannot

@@ -670,6 +670,7 @@ sv_status sv_batch_create(const sv_instance* inst, int32_t n, void* stream, sv_b
     B.contrib_off = B.op_off;
     B.grp_off = (int64_t)groups.size();
     B.theta_off = theta_off;
+    B.grad_off = theta_off;
     B.seg_off = (int64_t)segs.size();
     B.pp_off = (int64_t)pptr.size();
     theta_off += hc.n_params;

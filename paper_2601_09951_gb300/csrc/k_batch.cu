@@ -255,7 +255,7 @@ __device__ void run_instance(const BatchArgs& a, int idx, const Team& T, TeamS& 
   Rot* coef = a.coef + I.coef_off;
   double* contrib = a.contrib + I.contrib_off;
   double* theta = a.theta + I.theta_off;
-  double* grad = a.grad + I.theta_off;
+  double* grad = a.grad + I.grad_off;
   const int tid = T.rank;
   const int TS = T.size;
   const int hl = n < 6 ? n : 6;

@@ -59,9 +59,10 @@ struct BInst {
   uint64_t ref;
   int64_t op_off, grp_off, theta_off, seg_off, pp_off, etraj_off;
   int64_t coef_off, contrib_off;  // scratch offsets (Rot / double units)
+  int64_t grad_off;               // gradient offset (double units)
   double lr;
 };
-static_assert(sizeof(BInst) == 112, "BInst layout");
+static_assert(sizeof(BInst) == 120, "BInst layout");
 
 // A work item of the batched kernel: one instance on the CTA's 8 warps (cls 0, n <= 12), two
 // instances on 4 warps each (cls 1, n <= 11) or eight on one warp each (cls 2, n <= 9); unused

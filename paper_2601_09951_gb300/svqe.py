@@ -93,6 +93,12 @@ def lib():
         "sv_batch_run_dev": ([P, P, P, P], i32),
         "sv_batch_vqe_dev": ([P, P, dbl, i32, P], i32),
         "sv_adjoint_grad_noalloc": ([P, u64, P, i32, P, P, P, P, P], i32),
+        "sv_server_create": ([P, P], i32),
+        "sv_server_submit": ([P, P, P, i32, dbl, P], i32),
+        "sv_server_wait": ([P, u64, i32, P, P, P], i32),
+        "sv_server_cancel": ([P, u64], i32),
+        "sv_server_get_stats": ([P, P], i32),
+        "sv_server_destroy": ([P], i32),
     }
     for name, (args, res) in sigs.items():
         fn = getattr(L, name)
@@ -365,6 +371,84 @@ class Batch:
         if self._b:
             lib().sv_batch_free(self._b)
             self._b = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class _ServerConfig(ctypes.Structure):
+    _fields_ = [("hbm_budget_bytes", ctypes.c_uint64), ("max_active_small", ctypes.c_int32),
+                ("steps_per_tick", ctypes.c_int32), ("max_active_large", ctypes.c_int32),
+                ("serial", ctypes.c_int32)]
+
+
+class RequestInfo(ctypes.Structure):
+    _fields_ = [("id", ctypes.c_uint64), ("status", ctypes.c_int32),
+                ("n_qubits", ctypes.c_int32), ("n_params", ctypes.c_int32),
+                ("n_steps", ctypes.c_int32), ("footprint_bytes", ctypes.c_uint64),
+                ("submit_s", ctypes.c_double), ("admit_s", ctypes.c_double),
+                ("done_s", ctypes.c_double)]
+
+
+class ServerStats(ctypes.Structure):
+    _fields_ = [("submitted", ctypes.c_uint64), ("completed", ctypes.c_uint64),
+                ("failed", ctypes.c_uint64), ("cancelled", ctypes.c_uint64),
+                ("launches", ctypes.c_uint64), ("bytes_in_use", ctypes.c_uint64),
+                ("peak_bytes_in_use", ctypes.c_uint64), ("queued", ctypes.c_int32),
+                ("running", ctypes.c_int32)]
+
+
+class Server:
+    """The continuous-batching request loop (sv_server_*)."""
+
+    def __init__(self, hbm_budget_bytes=0, max_active_small=0, steps_per_tick=0,
+                 max_active_large=0, serial=False):
+        self._s = ctypes.c_void_p()
+        cfg = _ServerConfig(int(hbm_budget_bytes), int(max_active_small), int(steps_per_tick),
+                            int(max_active_large), 1 if serial else 0)
+        _check(lib().sv_server_create(ctypes.byref(cfg), ctypes.byref(self._s)))
+        self._meta = {}
+
+    def submit(self, inst, n_steps, lr, theta0=None):
+        C = Circuit(inst["circuit"])
+        H = PauliSum(inst["ham"], C.n)
+        one = _Instance()
+        one.circuit = C.struct
+        one.ham = H.struct
+        one.ref = int(inst["ref"])
+        th = np.ascontiguousarray(inst["theta"] if theta0 is None else theta0, dtype=np.float64)
+        rid = ctypes.c_uint64()
+        _check(lib().sv_server_submit(self._s, ctypes.byref(one), _ptr(th) if th.size else None,
+                                      int(n_steps), float(lr), ctypes.byref(rid)))
+        self._meta[rid.value] = (C.n_params, int(n_steps))
+        return rid.value
+
+    def wait(self, rid, timeout_ms=-1):
+        """(theta_final, energies[n_steps], RequestInfo); raises SvError on failure/timeout."""
+        P, T = self._meta[rid]
+        th = np.zeros(max(P, 1))
+        es = np.zeros(max(T, 1))
+        info = RequestInfo()
+        _check(lib().sv_server_wait(self._s, int(rid), int(timeout_ms), _ptr(th), _ptr(es),
+                                    ctypes.byref(info)))
+        del self._meta[rid]
+        return th[:P], es[:T], info
+
+    def cancel(self, rid):
+        _check(lib().sv_server_cancel(self._s, int(rid)))
+
+    def stats(self):
+        st = ServerStats()
+        _check(lib().sv_server_get_stats(self._s, ctypes.byref(st)))
+        return st
+
+    def close(self):
+        if self._s:
+            lib().sv_server_destroy(self._s)
+            self._s = ctypes.c_void_p()
 
     def __del__(self):
         try:
