@@ -39,10 +39,13 @@ def parse():
     ap.add_argument("--seed", type=int, default=1002)
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="batch", choices=["batch", "serve"],
+    ap.add_argument("--workload", default="batch",
+                    choices=["batch", "serve", "kernels", "single"],
                     help="batch: the batched evaluation step (default); serve: the request "
                          "loop (latency percentiles), printed as its own JSON line")
     ap.add_argument("--requests", type=int, default=300)
+    ap.add_argument("--qubits", type=int, default=28)
+    ap.add_argument("--ansatz", default="hea", choices=["hea", "uccsd"])
     return ap.parse_args()
 
 
@@ -226,15 +229,145 @@ def run_serve(args):
     print(json.dumps(line), flush=True)
 
 
+HBM_PEAK_GBS = 6678.2  # measured copy bandwidth (read + write) on the GB300s
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured"
+    except Exception:
+        return HBM_PEAK_GBS, "measured (copy, recorded in DESIGN.md)"
+
+
+def run_kernels(args):
+    """Per-kernel timing on the single-state path at n qubits (state larger than L2): each
+    kernel type through the public API, CUDA events on the context's stream, algorithmic bytes
+    and FP64 flops per amplitude (the per-row figures in the design doc)."""
+    import torch
+    torch.cuda.set_device(0)
+    from paper_2601_09951_gb300 import build as libbuild
+    libbuild.build()
+    from paper_2601_09951_gb300 import svqe
+    from paper_2601_09951_gb300 import workloads as W
+    n = args.qubits
+    N = 1 << n
+    stream = torch.cuda.Stream()
+    ctx = svqe.Context(n, stream=stream.cuda_stream)
+    peak, src = _peaks()
+
+    def one(gtype, wires, param=True):
+        cb = W.CircuitBuilder(n)
+        cb.add(gtype, wires, param="new" if param else None)
+        return svqe.Circuit(cb.build())
+
+    rows = {}
+
+    def timed(name, fn, bytes_per_amp, flops_per_amp, reps=5):
+        for _ in range(2):
+            fn()
+        torch.cuda.synchronize()
+        t0 = torch.cuda.Event(enable_timing=True)
+        t1 = torch.cuda.Event(enable_timing=True)
+        t0.record(stream)
+        for _ in range(reps):
+            fn()
+        t1.record(stream)
+        torch.cuda.synchronize()
+        ms = t0.elapsed_time(t1) / reps
+        gbs = bytes_per_amp * N / ms / 1e6
+        tf = flops_per_amp * N / ms / 1e9
+        rows[name] = {"ms": ms, "bytes_per_amp": bytes_per_amp, "GB/s": gbs,
+                      "hbm_frac": gbs / peak, "fp64_flops_per_amp": flops_per_amp,
+                      "fp64_TFLOP/s": tf, "fp64_frac": tf / FP64_PEAK_TFLOPS}
+
+    th = np.array([0.37])
+    low, mid, high = n - 1, n // 2, 0  # qubit n-1 is bit 0
+    timed("init_basis (a1)", lambda: ctx.init_reference(0), 16, 0)
+    for q, tag in ((low, "bit0"), (mid, "mid"), (high, "top")):
+        c = one(W.RY, [q])
+        timed(f"RY {tag} (a2)", lambda c=c: ctx.apply_circuit(c, th), 32, 6)
+    c = one(W.RZ, [mid])
+    timed("RZ mid (a2)", lambda: ctx.apply_circuit(c, th), 32, 6)
+    c = one(W.CNOT, [mid, low], param=False)
+    timed("CNOT (a3)", lambda: ctx.apply_circuit(c, np.zeros(0)), 16, 0)
+    c = one(W.SINGLE_EXC, [mid, low])
+    timed("SingleExcitation (a4)", lambda: ctx.apply_circuit(c, th), 16, 3)
+    c = one(W.DOUBLE_EXC, [high, mid, mid + 1, low])
+    timed("DoubleExcitation (a5)", lambda: ctx.apply_circuit(c, th), 4, 0.75)
+    layer = W.hea_circuit(n, 1, ring=True)
+    lc = svqe.Circuit(layer)
+    lth = np.random.default_rng(0).uniform(-3, 3, layer["n_params"])
+    # one HEA layer, fused passes: FP64 per amplitude = 6 per RY + 12 for the RZ run
+    n_pass, _ = svqe.circuit_plan(lc)
+    timed(f"fused HEA layer, {n_pass} passes (a6, forward)",
+          lambda: ctx.apply_circuit(lc, lth), 32 * n_pass, 6 * n + 12)
+    inst = W.hea_single(n, layers=1, n_terms=100)
+    H = svqe.Ham(ctx, inst["ham"])
+    G = H.info()[0]
+    timed(f"expval {G} groups (a7)", lambda: ctx.expval(H), 16 * G + 16, 4 * G + 4)
+    c1 = svqe.Circuit(inst["circuit"])
+    th1 = np.asarray(inst["theta"])
+    e_d = torch.zeros(1, dtype=torch.float64, device="cuda")
+    g_d = torch.zeros(c1.n_params, dtype=torch.float64, device="cuda")
+    th_d = torch.tensor(th1, device="cuda")
+    timed("adjoint energy+gradient, 1 HEA layer (a8+a9)",
+          lambda: ctx.adjoint_grad_dev(c1, th_d.data_ptr(), H, e_d.data_ptr(), g_d.data_ptr()),
+          0, 0, reps=3)
+    print(json.dumps({"metric": "single-state kernel throughput", "n_qubits": n,
+                      "state_bytes": 16 * N, "hbm_peak_GBps": peak, "hbm_peak_source": src,
+                      "fp64_peak_TFLOPs": FP64_PEAK_TFLOPS, "kernels": rows}), flush=True)
+
+
+def run_single(args):
+    """Energy + adjoint gradient evaluations of one state: the UCCSD-shaped 20-qubit circuit
+    (400 Givens gates, 2000 terms) or the hardware-efficient sweep at n qubits (10 layers,
+    100 random strings), evals/s with CUDA events on the context's stream."""
+    import torch
+    torch.cuda.set_device(0)
+    from paper_2601_09951_gb300 import build as libbuild
+    libbuild.build()
+    from paper_2601_09951_gb300 import svqe
+    from paper_2601_09951_gb300 import workloads as W
+    inst = W.uccsd_instance() if args.ansatz == "uccsd" else W.hea_single(args.qubits)
+    n = inst["circuit"]["n"]
+    stream = torch.cuda.Stream()
+    ctx = svqe.Context(n, stream=stream.cuda_stream)
+    ctx.init_reference(inst["ref"])
+    H = svqe.Ham(ctx, inst["ham"])
+    C = svqe.Circuit(inst["circuit"])
+    th_d = torch.tensor(np.asarray(inst["theta"]), device="cuda")
+    e_d = torch.zeros(1, dtype=torch.float64, device="cuda")
+    g_d = torch.zeros(max(C.n_params, 1), dtype=torch.float64, device="cuda")
+    call = lambda: ctx.adjoint_grad_dev(C, th_d.data_ptr(), H, e_d.data_ptr(), g_d.data_ptr())
+    for _ in range(max(1, args.warmup)):
+        call()
+    torch.cuda.synchronize()
+    reps = max(1, args.steps)
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    t0.record(stream)
+    for _ in range(reps):
+        call()
+    t1.record(stream)
+    torch.cuda.synchronize()
+    ms = t0.elapsed_time(t1) / reps
+    print(json.dumps({"metric": "single-state energy+adjoint-gradient evals/s",
+                      "workload": inst["name"], "n_qubits": n, "gates": len(C.gates),
+                      "terms": len(inst["ham"]["coeff"]), "groups": H.info()[0],
+                      "ms_per_eval": ms, "value": 1e3 / ms, "unit": "evals/s",
+                      "dtype": "f64"}), flush=True)
+
+
 def main():
     args = parse()
     rank, world, local = dist_env()
     if args.impl == "reference":
         run_reference(args)
         return
-    if args.workload == "serve":
+    if args.workload != "batch":
         if rank == 0:
-            run_serve(args)
+            {"serve": run_serve, "kernels": run_kernels, "single": run_single}[args.workload](args)
         return
     import torch
     torch.cuda.set_device(local)

@@ -147,6 +147,14 @@ sv_status sv_ham_info(const sv_ham* h, int32_t* n_groups, uint64_t* device_bytes
 sv_status sv_ham_lower(const sv_paulisum* h, int32_t kmax, int32_t* n_groups, int64_t* n_table,
                        uint64_t* x, uint64_t* zu, int32_t* cls, int64_t* toff, double* table);
 
+/* Host-only inspection of the fused-pass plan the single-state path uses for registers of at
+ * least 14 qubits (no device work): *n_passes receives the number of shared-memory passes
+ * over the state and, if pass_of_gate is not NULL, pass_of_gate[g] the pass that applies gate
+ * g (n_gates entries).  Gates keep their relative order whenever they share a qubit.
+ * tile_bits <= 0 selects the library's tile size (11 bits). */
+sv_status sv_circuit_plan(const sv_circuit* circuit, int32_t tile_bits, int32_t* n_passes,
+                          int32_t* pass_of_gate);
+
 /* ---------------------------------------------------------------- one state */
 
 /* psi = |basis_index> (Eq. 4); also records it as the context's reference state, the

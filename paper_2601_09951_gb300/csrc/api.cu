@@ -302,6 +302,33 @@ sv_status sv_ham_lower(const sv_paulisum* h, int32_t kmax, int32_t* n_groups, in
   return SV_OK;
 }
 
+sv_status sv_circuit_plan(const sv_circuit* circ, int32_t tile_bits, int32_t* n_passes,
+                          int32_t* pass_of_gate) {
+  clear_error();
+  if (!n_passes) { set_error("NULL argument"); return SV_EINVAL; }
+  HostCircuit hc;
+  sv_status st = lower_circuit(circ, 0, hc);
+  if (st != SV_OK) return st;
+  if (tile_bits <= 0) tile_bits = fused_tile_bits();
+  if (tile_bits < kMinLowBits + 4 || tile_bits > 11) {
+    set_error("tile_bits %d outside [%d, 11]", tile_bits, kMinLowBits + 4);
+    return SV_EINVAL;
+  }
+  HostPlan plan;
+  plan_passes(hc.ops, hc.n, tile_bits, plan);
+  *n_passes = (int32_t)plan.passes.size();
+  if (pass_of_gate) {
+    for (size_t p = 0; p < plan.passes.size(); ++p) {
+      const FPass& P = plan.passes[p];
+      for (int i = 0; i < P.n_items; ++i) {
+        const FItem& it = plan.items[P.first_item + i];
+        for (int g = 0; g < it.count; ++g) pass_of_gate[it.op + g] = (int32_t)p;
+      }
+    }
+  }
+  return SV_OK;
+}
+
 // ------------------------------------------------------------------------------ one state
 sv_status sv_init_reference(sv_ctx* c, uint64_t b) {
   clear_error();

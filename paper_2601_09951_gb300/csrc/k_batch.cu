@@ -37,6 +37,8 @@ struct TeamS {
   double2 cs[kM];
   int rz_op[kM];
   int rz_bit[kM];
+  uint32_t cz_mask[kM];  // both-bits masks of the segment's CZ gates
+  int n_cz;
 };
 
 // A team of nw warps running one instance.  Teams of one warp synchronise with __syncwarp,
@@ -192,18 +194,25 @@ __device__ __forceinline__ void op_pass(const Team& T, double2* v, uint32_t N, c
   }
 }
 
-// Build the diagonal segment's half tables: th[hi] * tl[lo] = prod_RZ e^{-i phi s(k)}.
+// Build the diagonal segment's half tables: th[hi] * tl[lo] = prod_RZ e^{-i phi s(k)}, and
+// the list of its CZ masks.
 __device__ __forceinline__ int diag_setup(const Team& T, TeamS& S, const DOp* ops,
                                           const Seg& sg, const double* theta, int n) {
-  int m = 0;
-  for (int l = 0; l < sg.count; ++l)
-    if (ops[sg.first + l].type == SV_GATE_RZ) {
+  int m = 0, ncz = 0;
+  for (int l = 0; l < sg.count; ++l) {
+    const int type = ops[sg.first + l].type;
+    if (type == SV_GATE_RZ) {
       if (T.rank == 0) {
         S.rz_op[m] = sg.first + l;
         S.rz_bit[m] = ops[sg.first + l].bit0;
       }
       ++m;
+    } else if (type == SV_GATE_CZ && ncz < kM) {
+      if (T.rank == 0) S.cz_mask[ncz] = (uint32_t)ops[sg.first + l].lo_or;
+      ++ncz;
     }
+  }
+  if (T.rank == 0) S.n_cz = ncz;
   T.sync();
   if (T.rank < m) {
     const DOp op = ops[S.rz_op[T.rank]];
@@ -233,12 +242,9 @@ __device__ __forceinline__ int diag_setup(const Team& T, TeamS& S, const DOp* op
 }
 
 // Sign of the CZ gates of a diagonal segment at amplitude k (true = negative).
-__device__ __forceinline__ bool cz_sign(const DOp* ops, const Seg& sg, uint32_t k) {
+__device__ __forceinline__ bool cz_sign(const TeamS& S, int ncz, uint32_t k) {
   uint32_t par = 0;
-  for (int l = 0; l < sg.count; ++l) {
-    const DOp& op = ops[sg.first + l];
-    if (op.type == SV_GATE_CZ) par ^= ((k & (uint32_t)op.lo_or) == (uint32_t)op.lo_or);
-  }
+  for (int c = 0; c < ncz; ++c) par ^= ((k & S.cz_mask[c]) == S.cz_mask[c]);
   return par & 1u;
 }
 
@@ -281,10 +287,11 @@ __device__ void run_instance(const BatchArgs& a, int idx, const Team& T, TeamS& 
       }
       if (sg.kind == SEG_DIAG) {
         diag_setup(T, S, ops, sg, theta, n);
+        const int ncz = S.n_cz;
         for (uint32_t k = tid; k < N; k += TS) {
           const double2 ph = cmul(S.th[k >> hl], S.tl[k & lmask]);
           double2 v = cmul(psi[k], ph);
-          if (cz_sign(ops, sg, k)) v = make_double2(dneg(v.x), dneg(v.y));
+          if (ncz && cz_sign(S, ncz, k)) v = make_double2(dneg(v.x), dneg(v.y));
           psi[k] = v;
         }
         T.sync();
@@ -415,25 +422,35 @@ __device__ void run_instance(const BatchArgs& a, int idx, const Team& T, TeamS& 
         }
       } else {  // SEG_DIAG
         const int m = diag_setup(T, S, ops, sg, theta, n);
-        double W = 0.0;
+        const int ncz = S.n_cz;
+        // Signed sums per bit: the bits below log_size are fixed within a thread (one running
+        // sum W suffices); at most kHB higher bits vary across the thread's amplitudes.
+        constexpr int kHB = 4;
+        const int nhb = n - T.log_size;
+        double W = 0.0, hb[kHB] = {0.0, 0.0, 0.0, 0.0};
         for (uint32_t k = tid; k < N; k += TS) {
           const double2 pk = psi[k];
           double2 lk = lam[k];
           const double w = fma(lk.x, pk.y, dneg(lk.y) * pk.x);  // Im(conj(lambda) psi)
           W += w;
 #pragma unroll
-          for (int g = 0; g < kM; ++g)
-            if (g < m && S.rz_bit[g] >= T.log_size)
-              v[g] += ((k >> S.rz_bit[g]) & 1u) ? dneg(w) : w;
+          for (int q = 0; q < kHB; ++q)
+            if (q < nhb) hb[q] += ((k >> (T.log_size + q)) & 1u) ? dneg(w) : w;
           const double2 ph = cmul(S.th[k >> hl], S.tl[k & lmask]);
           lk = cmul_conj(lk, ph);
-          if (cz_sign(ops, sg, k)) lk = make_double2(dneg(lk.x), dneg(lk.y));
+          if (ncz && cz_sign(S, ncz, k)) lk = make_double2(dneg(lk.x), dneg(lk.y));
           lam[k] = lk;
         }
 #pragma unroll
-        for (int g = 0; g < kM; ++g)
-          if (g < m && S.rz_bit[g] < T.log_size)
-            v[g] = (((uint32_t)tid >> S.rz_bit[g]) & 1u) ? dneg(W) : W;
+        for (int g = 0; g < kM; ++g) {
+          if (g >= m) break;
+          const int b = S.rz_bit[g];
+          double val = (((uint32_t)tid >> (b < T.log_size ? b : 0)) & 1u) ? dneg(W) : W;
+#pragma unroll
+          for (int q = 0; q < kHB; ++q)
+            if (b == T.log_size + q) val = hb[q];
+          v[g] = val;
+        }
         const double tot = team_sum16(T, S, v, m);
         if (tid < m) contrib[S.rz_op[tid]] = tot;
       }

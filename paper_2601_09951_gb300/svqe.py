@@ -76,6 +76,7 @@ def lib():
         "sv_ham_free": ([P], i32),
         "sv_ham_info": ([P, P, P], i32),
         "sv_ham_lower": ([P, i32, P, P, P, P, P, P, P], i32),
+        "sv_circuit_plan": ([P, i32, P, P], i32),
         "sv_init_reference": ([P, u64], i32),
         "sv_apply_circuit": ([P, P, P], i32),
         "sv_expval_paulisum": ([P, P, P], i32),
@@ -173,6 +174,15 @@ def ham_lower(ham, n, kmax):
     _check(lib().sv_ham_lower(ps.ref(), int(kmax), ctypes.byref(ng), ctypes.byref(nt),
                               _ptr(x), _ptr(zu), _ptr(cls), _ptr(toff), _ptr(table)))
     return x, zu, cls, toff, table[:nt.value]
+
+
+def circuit_plan(circuit, tile_bits=0):
+    """Host-only fused-pass plan: (number of passes, pass index of every gate)."""
+    C = circuit if isinstance(circuit, Circuit) else Circuit(circuit)
+    npass = ctypes.c_int32()
+    pog = np.zeros(max(len(C.gates), 1), np.int32)
+    _check(lib().sv_circuit_plan(C.ref(), int(tile_bits), ctypes.byref(npass), _ptr(pog)))
+    return npass.value, pog[:len(C.gates)]
 
 
 GROUP_DTYPE = np.dtype([("x_mask", "<u8"), ("z_union", "<u8"), ("z_bits", "<i4"),

@@ -122,3 +122,34 @@ def test_lowering_rejects_bad_masks():
         svqe.ham_lower({"x": np.array([8], np.uint64), "z": np.array([0], np.uint64),
                         "coeff": np.array([1.0])}, 3, 3)
     assert e.value.status == svqe.SV_EINVAL
+
+
+def _gate_bits(circ, g):
+    k = W.N_WIRES[int(circ["types"][g])]
+    return {int(circ["n"]) - 1 - int(w) for w in circ["wires"][g][:k]}
+
+
+@pytest.mark.parametrize("make", [
+    lambda: W.hea_circuit(20, 3, ring=True),
+    lambda: W.hea_circuit(31, 2, ring=True),
+    lambda: W.uccsd_instance(n=20, n_elec=10, n_singles=40, n_doubles=60, n_terms=30)["circuit"],
+])
+def test_fused_plan_keeps_dependencies_and_fits_tiles(make):
+    """Host-side pass planner: a gate never moves ahead of an earlier gate it shares a qubit
+    with, and every pass's non-diagonal gates act inside an 11-bit tile that keeps 4 low bits."""
+    circ = make()
+    n_pass, pog = svqe.circuit_plan(circ)
+    G = len(circ["types"])
+    assert n_pass >= 1 and pog.min() == 0 and pog.max() == n_pass - 1
+    for a in range(G):
+        for b in range(a + 1, G):
+            if _gate_bits(circ, a) & _gate_bits(circ, b):
+                assert pog[a] <= pog[b], (a, b, pog[a], pog[b])
+    for p in range(n_pass):
+        bits = set()
+        for g in np.flatnonzero(pog == p):
+            if int(circ["types"][g]) != W.RZ:   # RZ runs are diagonal items: any bits
+                bits |= _gate_bits(circ, g)
+        assert len(bits | {0, 1, 2, 3}) <= 11, (p, sorted(bits))
+    # fusion actually fuses: far fewer passes than gates
+    assert n_pass * 3 <= G
