@@ -38,6 +38,9 @@ def lib():
         L.orc_energy.restype = i32
         L.orc_energy_grad.argtypes = [i32, u64, i32, P, P, P, P, P, i32, i32, P, P, P, P, P]
         L.orc_energy_grad.restype = i32
+        L.orc_energy_grad_subset.argtypes = [i32, u64, i32, P, P, P, P, P, i32, i32, P, P, P,
+                                             P, i32, P, P]
+        L.orc_energy_grad_subset.restype = i32
         L.orc_state.argtypes = [i32, u64, i32, P, P, P, P, P, P]
         L.orc_state.restype = i32
         L.orc_set_threads.argtypes = [i32]
@@ -160,6 +163,26 @@ def energy_grad(inst, theta=None):
     if rc != 0:
         raise ValueError(f"oracle gradient failed ({rc})")
     return e.value, g[:n_params]
+
+
+def energy_grad_subset(inst, which, theta=None):
+    """(E, {p: dE/dtheta_p}) for the parameters in `which` only (same shift rules)."""
+    circ, ham = inst["circuit"], inst["ham"]
+    theta = inst["theta"] if theta is None else theta
+    types, wires, params, fixed = _circ(circ)
+    x, z, c = _ham(ham)
+    th = np.ascontiguousarray(theta, dtype=np.float64)
+    n_params = int(circ["n_params"])
+    w = np.ascontiguousarray(list(which), dtype=np.int32)
+    g = np.zeros(max(n_params, 1), dtype=np.float64)
+    e = ctypes.c_double()
+    rc = lib().orc_energy_grad_subset(int(circ["n"]), int(inst["ref"]), len(types), _p(types),
+                                      _p(wires), _p(params), _p(fixed),
+                                      _p(th) if th.size else None, n_params, len(c), _p(x),
+                                      _p(z), _p(c), _p(w), len(w), ctypes.byref(e), _p(g))
+    if rc != 0:
+        raise ValueError(f"oracle gradient failed ({rc})")
+    return e.value, {int(p): float(g[p]) for p in w}
 
 
 def gd_trajectory(inst, lr, n_steps, theta0=None):

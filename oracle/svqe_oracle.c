@@ -242,10 +242,43 @@ int orc_get_threads(void) { return g_threads; }
  * the second being the shift rule for a generator with eigenvalues {-1/2, 0, 1/2}.  The
  * shifted energies are independent circuit evaluations; they run in parallel (one state
  * buffer per thread) and are summed afterwards in a fixed order. */
+static int energy_grad_impl(int n, uint64_t ref, int n_gates, const int* types,
+                            const int* wires, const int* params, const double* fixed,
+                            const double* theta, int n_params, int n_terms, const uint64_t* x,
+                            const uint64_t* z, const double* coeff, const char* want,
+                            double* e, double* grad);
+
 int orc_energy_grad(int n, uint64_t ref, int n_gates, const int* types, const int* wires,
                     const int* params, const double* fixed, const double* theta, int n_params,
                     int n_terms, const uint64_t* x, const uint64_t* z, const double* coeff,
                     double* e, double* grad) {
+  return energy_grad_impl(n, ref, n_gates, types, wires, params, fixed, theta, n_params,
+                          n_terms, x, z, coeff, NULL, e, grad);
+}
+
+/* As orc_energy_grad, for the parameters listed in `which` only (n_which entries); grad has
+ * n_params entries, the others are left at zero.  Used to sample gradients of circuits too
+ * large for the full parameter-shift sweep. */
+int orc_energy_grad_subset(int n, uint64_t ref, int n_gates, const int* types, const int* wires,
+                           const int* params, const double* fixed, const double* theta,
+                           int n_params, int n_terms, const uint64_t* x, const uint64_t* z,
+                           const double* coeff, const int* which, int n_which, double* e,
+                           double* grad) {
+  char* want = (char*)calloc(n_params > 0 ? n_params : 1, 1);
+  if (!want) return -2;
+  for (int k = 0; k < n_which; ++k)
+    if (which[k] >= 0 && which[k] < n_params) want[which[k]] = 1;
+  const int rc = energy_grad_impl(n, ref, n_gates, types, wires, params, fixed, theta, n_params,
+                                  n_terms, x, z, coeff, want, e, grad);
+  free(want);
+  return rc;
+}
+
+static int energy_grad_impl(int n, uint64_t ref, int n_gates, const int* types,
+                            const int* wires, const int* params, const double* fixed,
+                            const double* theta, int n_params, int n_terms, const uint64_t* x,
+                            const uint64_t* z, const double* coeff, const char* want,
+                            double* e, double* grad) {
   const double PI = 3.14159265358979323846;
   const double d1 = (sqrt(2.0) + 1.0) / (4.0 * sqrt(2.0));
   const double d2 = (sqrt(2.0) - 1.0) / (4.0 * sqrt(2.0));
@@ -253,6 +286,7 @@ int orc_energy_grad(int n, uint64_t ref, int n_gates, const int* types, const in
   for (int g = 0; g < n_gates; ++g) {
     if (params[g] < 0 || !is_param_gate(types[g])) continue;
     if (params[g] >= n_params) return -1;
+    if (want && !want[params[g]]) continue;
     n_jobs += (types[g] == ORC_SINGLE_EXC || types[g] == ORC_DOUBLE_EXC) ? 4 : 2;
   }
   int* jg = (int*)malloc(sizeof(int) * n_jobs);
@@ -264,6 +298,7 @@ int orc_energy_grad(int n, uint64_t ref, int n_gates, const int* types, const in
   jg[k] = -1; js[k] = 0; jw[k] = 0; ++k;
   for (int g = 0; g < n_gates; ++g) {
     if (params[g] < 0 || !is_param_gate(types[g])) continue;
+    if (want && !want[params[g]]) continue;
     if (types[g] == ORC_SINGLE_EXC || types[g] == ORC_DOUBLE_EXC) {
       jg[k] = g; js[k] = +0.5 * PI; jw[k] = +d1; ++k;
       jg[k] = g; js[k] = -0.5 * PI; jw[k] = -d1; ++k;

@@ -305,3 +305,12 @@ def test_uccsd_generator_shape():
     assert np.sum(inst["circuit"]["types"] == W.DOUBLE_EXC) == 320
     pairs = set(zip(inst["ham"]["x"].tolist(), inst["ham"]["z"].tolist()))
     assert len(pairs) == 2000
+
+
+def test_gradient_subset_equals_full_sweep_entries():
+    inst = W.uccsd_instance(n=8, n_elec=4, n_singles=6, n_doubles=6, n_terms=80, seed=12)
+    e, g = oracle.energy_grad(inst)
+    es, gs = oracle.energy_grad_subset(inst, [0, 5, 11])
+    assert es == e
+    for p, v in gs.items():
+        assert v == g[p]
