@@ -162,10 +162,19 @@ int segment_ops(const std::vector<DOp>& ops, int min_layer, int min_diag_rz,
       if (e - l >= min_layer) segs.push_back(Seg{SEG_RLAYER, l, e - l, ckpt++});
       else push_gates(l, e - l);
       l = e;
+    } else if (t == SV_GATE_CNOT || t == SV_GATE_X) {
+      int e = l;
+      while (e < n_ops && (ops[e].type == SV_GATE_CNOT || ops[e].type == SV_GATE_X) &&
+             e - l < kMaxPerm)
+        ++e;
+      if (e - l >= 2) segs.push_back(Seg{SEG_PERM, l, e - l, ckpt++});
+      else push_gates(l, e - l);
+      l = e;
     } else {
       int e = l;
       while (e < n_ops && ops[e].type != SV_GATE_RZ && ops[e].type != SV_GATE_CZ &&
-             ops[e].type != SV_GATE_RY && ops[e].type != SV_GATE_RX)
+             ops[e].type != SV_GATE_RY && ops[e].type != SV_GATE_RX &&
+             ops[e].type != SV_GATE_CNOT && ops[e].type != SV_GATE_X)
         ++e;
       push_gates(l, e - l);
       l = e;

@@ -39,7 +39,10 @@ struct TeamS {
   int rz_bit[kM];
   uint32_t cz_mask[kM];  // both-bits masks of the segment's CZ gates
   int n_cz;
+  uint32_t perm_lo[kMaxPerm];  // condition and flip masks of a permutation segment's gates
+  uint32_t perm_fl[kMaxPerm];
 };
+
 
 // A team of nw warps running one instance.  Teams of one warp synchronise with __syncwarp,
 // larger teams with named barrier `bar` (barrier 0 is the CTA-wide one).
@@ -53,6 +56,15 @@ struct Team {
     }
   }
 };
+
+// Stage a permutation segment's (condition, flip) masks in shared memory.
+__device__ __forceinline__ void perm_setup(const Team& T, TeamS& S, const DOp* ops, const Seg& sg) {
+  if (T.rank < sg.count) {
+    S.perm_lo[T.rank] = (uint32_t)ops[sg.first + T.rank].lo_or;
+    S.perm_fl[T.rank] = (uint32_t)ops[sg.first + T.rank].flip;
+  }
+  T.sync();
+}
 
 __device__ __forceinline__ uint32_t insert_zeros32(uint32_t p, const uint8_t* sb, int k) {
 #pragma unroll
@@ -194,6 +206,37 @@ __device__ __forceinline__ void op_pass(const Team& T, double2* v, uint32_t N, c
   }
 }
 
+// Apply two single-qubit ops on distinct bits in one pass: each thread takes the four
+// amplitudes of a block (both bits 0, either, both 1), rotates them for the first op, then for
+// the second, in registers.  Half the barriers and shared-memory traffic of two op_pass calls.
+__device__ __forceinline__ void op_pass2(const Team& T, double2* v, uint32_t N, const DOp& o1,
+                                         const Rot& r1, const DOp& o2, const Rot& r2, bool inv) {
+  const uint32_t b1 = (uint32_t)o1.flip, b2 = (uint32_t)o2.flip;
+  uint8_t sb[2];
+  sb[0] = (uint8_t)min(o1.bit0, o2.bit0);
+  sb[1] = (uint8_t)max(o1.bit0, o2.bit0);
+  const uint32_t nb = N >> 2;
+  for (uint32_t p = T.rank; p < nb; p += T.size) {
+    const uint32_t i = insert_zeros32(p, sb, 2);
+    double2 a = v[i], b = v[i | b1], c = v[i | b2], d = v[i | b1 | b2];
+    if (!inv) {
+      pair_apply(o1.type, r1, false, a, b);
+      pair_apply(o1.type, r1, false, c, d);
+      pair_apply(o2.type, r2, false, a, c);
+      pair_apply(o2.type, r2, false, b, d);
+    } else {
+      pair_apply(o2.type, r2, true, a, c);
+      pair_apply(o2.type, r2, true, b, d);
+      pair_apply(o1.type, r1, true, a, b);
+      pair_apply(o1.type, r1, true, c, d);
+    }
+    v[i] = a;
+    v[i | b1] = b;
+    v[i | b2] = c;
+    v[i | b1 | b2] = d;
+  }
+}
+
 // Build the diagonal segment's half tables: th[hi] * tl[lo] = prod_RZ e^{-i phi s(k)}, and
 // the list of its CZ masks.
 __device__ __forceinline__ int diag_setup(const Team& T, TeamS& S, const DOp* ops,
@@ -285,7 +328,20 @@ __device__ void run_instance(const BatchArgs& a, int idx, const Team& T, TeamS& 
         for (uint32_t k = tid; k < N; k += TS) dst[k] = psi[k];
         T.sync();
       }
-      if (sg.kind == SEG_DIAG) {
+      if (sg.kind == SEG_PERM) {
+        // psi'[j] = psi[P^-1 j] with P = C_last ... C_first (each CNOT/X is its own inverse)
+        perm_setup(T, S, ops, sg);
+        for (uint32_t j = tid; j < N; j += TS) {
+          uint32_t src = j;
+          for (int l = sg.count - 1; l >= 0; --l)
+            if ((src & S.perm_lo[l]) == S.perm_lo[l]) src ^= S.perm_fl[l];
+          lam[j] = psi[src];
+        }
+        T.sync();
+        double2* t = psi;
+        psi = lam;
+        lam = t;
+      } else if (sg.kind == SEG_DIAG) {
         diag_setup(T, S, ops, sg, theta, n);
         const int ncz = S.n_cz;
         for (uint32_t k = tid; k < N; k += TS) {
@@ -295,6 +351,16 @@ __device__ void run_instance(const BatchArgs& a, int idx, const Team& T, TeamS& 
           psi[k] = v;
         }
         T.sync();
+      } else if (sg.kind == SEG_RLAYER) {
+        int l = sg.first;
+        for (; l + 1 < sg.first + sg.count; l += 2) {
+          op_pass2(T, psi, N, ops[l], coef[l], ops[l + 1], coef[l + 1], false);
+          T.sync();
+        }
+        if (l < sg.first + sg.count) {
+          op_pass(T, psi, N, ops[l], coef[l], false);
+          T.sync();
+        }
       } else {
         for (int l = sg.first; l < sg.first + sg.count; ++l) {
           op_pass(T, psi, N, ops[l], coef[l], false);
@@ -389,6 +455,25 @@ __device__ void run_instance(const BatchArgs& a, int idx, const Team& T, TeamS& 
         }
         continue;
       }
+      if (sg.kind == SEG_PERM) {
+        // lambda_before[j] = lambda_after[P j], gathered into the psi buffer (psi is reloaded
+        // from the checkpoint below), then the buffers swap roles
+        perm_setup(T, S, ops, sg);
+        for (uint32_t j = tid; j < N; j += TS) {
+          uint32_t dst = j;
+          for (int l = 0; l < sg.count; ++l)
+            if ((dst & S.perm_lo[l]) == S.perm_lo[l]) dst ^= S.perm_fl[l];
+          psi[j] = lam[dst];
+        }
+        T.sync();
+        double2* t = psi;
+        psi = lam;
+        lam = t;
+        const double2* src = ck + (size_t)sg.ckpt * N;
+        for (uint32_t k = tid; k < N; k += TS) psi[k] = src[k];
+        T.sync();
+        continue;
+      }
       double v[kM];
 #pragma unroll
       for (int g = 0; g < kM; ++g) v[g] = 0.0;
@@ -415,8 +500,13 @@ __device__ void run_instance(const BatchArgs& a, int idx, const Team& T, TeamS& 
         }
         const double tot = team_sum16(T, S, v, sg.count);
         if (tid < sg.count) contrib[sg.first + tid] = tot;
-        // un-apply the layer to lambda
-        for (int l = sg.first + sg.count - 1; l >= sg.first; --l) {
+        // un-apply the layer to lambda (its gates commute: pairs in forward order, inverted)
+        int l = sg.first;
+        for (; l + 1 < sg.first + sg.count; l += 2) {
+          op_pass2(T, lam, N, ops[l], coef[l], ops[l + 1], coef[l + 1], true);
+          T.sync();
+        }
+        if (l < sg.first + sg.count) {
           op_pass(T, lam, N, ops[l], coef[l], true);
           T.sync();
         }

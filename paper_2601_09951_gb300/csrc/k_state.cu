@@ -69,7 +69,7 @@ __global__ void k_prep_coefs(const DOp* __restrict__ ops, int n_ops,
 }
 
 template <int KIND>
-__global__ void __launch_bounds__(kThreads) k_apply(double2* __restrict__ psi, uint64_t npairs,
+__global__ void __launch_bounds__(kThreads, 4) k_apply(double2* __restrict__ psi, uint64_t npairs,
                                                     DOp op, const Rot* __restrict__ coef,
                                                     int inv) {
   Rot r = *coef;

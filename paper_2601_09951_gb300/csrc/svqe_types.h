@@ -59,7 +59,10 @@ static_assert(sizeof(DGroup) == 32, "DGroup layout");
 //   SEG_DIAG  : RZ and CZ gates (diagonal, mutually commuting), applied as one phase
 //               e^{-i sum_q phi_q s_q(k)} (+-1 for CZ) per amplitude from two half tables;
 //               gradients from w_k = Im(conj(lambda_k) psi_k); psi reloaded from a checkpoint.
-enum { SEG_GATES = 0, SEG_RLAYER = 1, SEG_DIAG = 2 };
+//   SEG_PERM  : CNOT and X gates: their product is one permutation of basis indices, applied
+//               as a single gather into the other buffer (the psi and lambda buffers then swap
+//               roles); the sweep gathers lambda back and reloads psi from a checkpoint.
+enum { SEG_GATES = 0, SEG_RLAYER = 1, SEG_DIAG = 2, SEG_PERM = 3 };
 struct Seg {
   int32_t kind;
   int32_t first;  // first op
@@ -68,6 +71,8 @@ struct Seg {
 };
 static_assert(sizeof(Seg) == 16, "Seg layout");
 
+// Gates of one permutation segment of the batched kernel.
+constexpr int kMaxPerm = 32;
 // Gradient slots per fused pass (and RZ gates per diagonal item).
 constexpr int kMaxSlotsDev = 16;
 // Lowest contiguous bits every fused tile includes (runs of 2^kMinLowBits amplitudes).
