@@ -117,8 +117,9 @@ uint64_t sv_ctx_device_bytes(int32_t n_qubits);
 
 /* ---------------------------------------------------------------- contexts */
 
-/* Create a context for n_qubits in [1, 31].  cuda_stream is a cudaStream_t to order work on,
- * or NULL for a stream the context creates and owns.  Allocates psi and lambda (2 x 2^n x 16
+/* Create a context for n_qubits in [1, 31].  cuda_stream is a cudaStream_t to order work on
+ * (cudaStreamLegacy or cudaStreamPerThread for a default stream), or NULL for a stream the
+ * context creates and owns.  Allocates psi and lambda (2 x 2^n x 16
  * bytes) and scratch on the current device; SV_ENOMEM if that fails. */
 sv_status sv_create(sv_ctx** out, int32_t n_qubits, void* cuda_stream);
 /* Free a context and everything it allocated (NULL is accepted). */
@@ -224,6 +225,15 @@ sv_status sv_batch_run_dev(sv_batch* b, const double* theta_dev, double* energy_
  * each update, or may be NULL.  Stream-ordered. */
 sv_status sv_batch_vqe_dev(sv_batch* b, double* theta_dev, double lr, int32_t n_steps,
                            double* energy_traj_dev);
+
+/* n_steps of Adam, the paper's optimizer (Sec. 3.4; Algorithm 1's update), on every instance
+ * inside one persistent launch: m <- b1 m + (1-b1) g, v <- b2 v + (1-b2) g^2,
+ * theta <- theta - lr * (m / (1 - b1^t)) / (sqrt(v / (1 - b2^t)) + eps) with b1 = 0.9,
+ * b2 = 0.999, eps = 1e-8 and t the update count.  The moments live in the batch; reset = 1
+ * starts from zero moments and t = 0, reset = 0 continues from the previous call (the first
+ * call always resets).  energy_traj_dev as for sv_batch_vqe_dev.  Stream-ordered. */
+sv_status sv_batch_adam_dev(sv_batch* b, double* theta_dev, double lr, int32_t n_steps,
+                            double* energy_traj_dev, int32_t reset);
 
 /* ---------------------------------------------------------------- serving */
 

@@ -198,3 +198,24 @@ def gd_trajectory(inst, lr, n_steps, theta0=None):
         ths.append(theta.copy())
         theta = theta - lr * g
     return np.array(es), np.array(gs), np.array(ths), theta
+
+
+def adam_trajectory(inst, lr, n_steps, theta0=None, beta1=0.9, beta2=0.999, eps=1e-8):
+    """Adam, the optimizer of the paper's loop (Sec. 3.4; Algorithm 1's update), on the
+    parameter-shift gradient: m <- b1 m + (1-b1) g, v <- b2 v + (1-b2) g^2,
+    theta <- theta - lr * (m / (1 - b1^t)) / (sqrt(v / (1 - b2^t)) + eps), t = 1, 2, ...
+    Returns (E_t, theta_t) before each update and the final theta."""
+    theta = np.array(inst["theta"] if theta0 is None else theta0, dtype=np.float64)
+    m = np.zeros_like(theta)
+    v = np.zeros_like(theta)
+    es, ths = [], []
+    for t in range(1, n_steps + 1):
+        e, g = energy_grad(inst, theta)
+        es.append(e)
+        ths.append(theta.copy())
+        m = beta1 * m + (1.0 - beta1) * g
+        v = beta2 * v + (1.0 - beta2) * g * g
+        mh = m / (1.0 - beta1 ** t)
+        vh = v / (1.0 - beta2 ** t)
+        theta = theta - lr * mh / (np.sqrt(vh) + eps)
+    return np.array(es), np.array(ths), theta

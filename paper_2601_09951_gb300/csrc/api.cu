@@ -85,6 +85,9 @@ struct sv_batch {
   double* theta = nullptr;   // owned buffers for the host-pointer entry point
   double* energy = nullptr;
   double* grad = nullptr;
+  double* adam_m = nullptr;  // Adam moments (allocated on first use) and updates taken
+  double* adam_v = nullptr;
+  int adam_t = 0;
   double flops = 0.0;        // algorithmic FP64 flops of one run (sv_batch_cost)
   double bytes = 0.0;        // algorithmic HBM bytes of one run
   // CUDA graph of [counter reset, persistent kernel] for one set of device pointers
@@ -642,6 +645,8 @@ sv_status sv_batch_free(sv_batch* b) {
   cudaFree(b->theta);
   cudaFree(b->energy);
   cudaFree(b->grad);
+  cudaFree(b->adam_m);
+  cudaFree(b->adam_v);
   if (b->own_stream && b->stream) cudaStreamDestroy(b->stream);
   cudaGetLastError();
   delete b;
@@ -835,6 +840,13 @@ static BatchArgs batch_args(sv_batch* b, double* theta, double* energy, double* 
   a.lr = lr;
   a.lr_inst = nullptr;
   a.etraj = etraj;
+  a.opt = 0;
+  a.adam_m = nullptr;
+  a.adam_v = nullptr;
+  a.adam_t0 = 0;
+  a.beta1 = 0.9;
+  a.beta2 = 0.999;
+  a.eps = 1e-8;
   return a;
 }
 
@@ -843,6 +855,13 @@ sv_status sv_batch_run_dev(sv_batch* b, const double* theta_dev, double* energy_
   clear_error();
   if (!b || !theta_dev || !energy_dev || !grad_dev) { set_error("NULL argument"); return SV_EINVAL; }
   SV_CHECK_STICKY(b);
+  if (b->stream == cudaStreamLegacy || b->stream == cudaStreamPerThread) {
+    // default streams cannot be captured: launch directly
+    SV_CUDA(cudaMemsetAsync(b->counter, 0, sizeof(int), b->stream), b);
+    SV_CUDA(launch_batch(batch_args(b, const_cast<double*>(theta_dev), energy_dev, grad_dev, 0,
+                                    0.0, nullptr), b->grid, b->smem, b->stream), b);
+    return SV_OK;
+  }
   const void* key[3] = {theta_dev, energy_dev, grad_dev};
   if (!b->exec || std::memcmp(key, b->key, sizeof key) != 0) {
     if (b->exec) { cudaGraphExecDestroy(b->exec); b->exec = nullptr; }
@@ -880,6 +899,38 @@ sv_status sv_batch_run(sv_batch* b, const double* theta, double* energy, double*
     SV_CUDA(cudaMemcpyAsync(grad, b->grad, b->total_params * sizeof(double),
                             cudaMemcpyDeviceToHost, b->stream), b);
   SV_CUDA(cudaStreamSynchronize(b->stream), b);
+  return SV_OK;
+}
+
+sv_status sv_batch_adam_dev(sv_batch* b, double* theta_dev, double lr, int32_t n_steps,
+                            double* energy_traj_dev, int32_t reset) {
+  clear_error();
+  if (!b || !theta_dev) { set_error("NULL argument"); return SV_EINVAL; }
+  if (n_steps < 1) { set_error("n_steps %d < 1", n_steps); return SV_EINVAL; }
+  SV_CHECK_STICKY(b);
+  const size_t P = (size_t)std::max<int64_t>(b->total_params, 1);
+  if (!b->adam_m) {
+    if (cudaMalloc((void**)&b->adam_m, P * sizeof(double)) != cudaSuccess ||
+        cudaMalloc((void**)&b->adam_v, P * sizeof(double)) != cudaSuccess) {
+      cudaGetLastError();
+      set_error("device allocation of Adam moments failed");
+      return SV_ENOMEM;
+    }
+    reset = 1;
+  }
+  if (reset) {
+    SV_CUDA(cudaMemsetAsync(b->adam_m, 0, P * sizeof(double), b->stream), b);
+    SV_CUDA(cudaMemsetAsync(b->adam_v, 0, P * sizeof(double), b->stream), b);
+    b->adam_t = 0;
+  }
+  BatchArgs a = batch_args(b, theta_dev, b->energy, b->grad, n_steps, lr, energy_traj_dev);
+  a.opt = 1;
+  a.adam_m = b->adam_m;
+  a.adam_v = b->adam_v;
+  a.adam_t0 = b->adam_t;
+  SV_CUDA(cudaMemsetAsync(b->counter, 0, sizeof(int), b->stream), b);
+  SV_CUDA(launch_batch(a, b->grid, b->smem, b->stream), b);
+  b->adam_t += n_steps;
   return SV_OK;
 }
 

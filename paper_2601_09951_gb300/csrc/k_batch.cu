@@ -370,10 +370,11 @@ __device__ void run_instance(const BatchArgs& a, int idx, const Team& T, TeamS& 
     }
 
     // ---------------------------------------------------------------- lambda = H psi
-    // Each thread carries kHU amplitudes through the group loop: kHU independent multiply-add
-    // chains and table loads in flight, one group-record load per kHU amplitudes.
+    // Each thread carries all of its amplitudes (at most kHU = 16 in every team class) through
+    // the group loop: kHU independent multiply-add chains and table loads in flight, and one
+    // group-record load per thread per group.
     double e = 0.0;
-    constexpr int kHU = 4;
+    constexpr int kHU = 16;
     for (uint32_t k0 = tid; k0 < N; k0 += kHU * TS) {
       double2 acc[kHU];
 #pragma unroll
@@ -478,22 +479,40 @@ __device__ void run_instance(const BatchArgs& a, int idx, const Team& T, TeamS& 
 #pragma unroll
       for (int g = 0; g < kM; ++g) v[g] = 0.0;
       if (sg.kind == SEG_RLAYER) {
-        // gradients of every gate from (psi, lambda) at the layer's end
-        for (int g = 0; g < sg.count; ++g) {
+        // gradients of every gate from (psi, lambda) at the layer's end, two gates per pass:
+        // each thread reads a block of four amplitudes of psi and lambda and accumulates both
+        // gates' pair terms from it
+        int g = 0;
+        for (; g + 1 < sg.count; g += 2) {
+          const DOp o1 = ops[sg.first + g], o2 = ops[sg.first + g + 1];
+          const uint32_t b1 = (uint32_t)o1.flip, b2 = (uint32_t)o2.flip;
+          uint8_t sb[2];
+          sb[0] = (uint8_t)min(o1.bit0, o2.bit0);
+          sb[1] = (uint8_t)max(o1.bit0, o2.bit0);
+          double a1 = 0.0, a2 = 0.0;
+          for (uint32_t p = tid; p < (N >> 2); p += TS) {
+            const uint32_t i = insert_zeros32(p, sb, 2);
+            const double2 pa = psi[i], pb = psi[i | b1], pc = psi[i | b2], pd = psi[i | b1 | b2];
+            const double2 la = lam[i], lb = lam[i | b1], lc = lam[i | b2], ld = lam[i | b1 | b2];
+            pair_grad_acc(o1.type, la, lb, pa, pb, a1);
+            pair_grad_acc(o1.type, lc, ld, pc, pd, a1);
+            pair_grad_acc(o2.type, la, lc, pa, pc, a2);
+            pair_grad_acc(o2.type, lb, ld, pb, pd, a2);
+          }
+#pragma unroll
+          for (int q = 0; q < kM; ++q) {
+            if (q == g) v[q] = a1;
+            if (q == g + 1) v[q] = a2;
+          }
+        }
+        if (g < sg.count) {
           const DOp op = ops[sg.first + g];
           const uint32_t fl = (uint32_t)op.flip;
-          double acc = 0.0, acc2 = 0.0;  // two chains: even and odd iterations
-          const uint32_t np = N >> 1;
-          for (uint32_t p = tid; p < np; p += 2 * TS) {
+          double acc = 0.0;
+          for (uint32_t p = tid; p < (N >> 1); p += TS) {
             const uint32_t i = insert_zeros32(p, op.sb, 1);
             pair_grad_acc(op.type, lam[i], lam[i ^ fl], psi[i], psi[i ^ fl], acc);
-            const uint32_t p2 = p + TS;
-            if (p2 < np) {
-              const uint32_t i2 = insert_zeros32(p2, op.sb, 1);
-              pair_grad_acc(op.type, lam[i2], lam[i2 ^ fl], psi[i2], psi[i2 ^ fl], acc2);
-            }
           }
-          acc += acc2;
 #pragma unroll
           for (int q = 0; q < kM; ++q)
             if (q == g) v[q] = acc;
@@ -556,7 +575,22 @@ __device__ void run_instance(const BatchArgs& a, int idx, const Team& T, TeamS& 
       for (int j = a.pptr[I.pp_off + p]; j < a.pptr[I.pp_off + p + 1]; ++j)
         g += contrib[a.pops[j]];
       grad[p] = g;
-      if (gd) theta[p] = fma(-lr, g, theta[p]);
+      if (gd) {
+        if (a.opt == 1) {
+          // Adam (the paper's optimizer, Sec. 3.4): bias-corrected moment estimates
+          const size_t q = (size_t)I.grad_off + p;
+          const double m = fma(a.beta1, a.adam_m[q], (1.0 - a.beta1) * g);
+          const double v = fma(a.beta2, a.adam_v[q], (1.0 - a.beta2) * g * g);
+          a.adam_m[q] = m;
+          a.adam_v[q] = v;
+          const int t = a.adam_t0 + step + 1;
+          const double mh = m / (1.0 - pow(a.beta1, (double)t));
+          const double vh = v / (1.0 - pow(a.beta2, (double)t));
+          theta[p] -= lr * mh / (sqrt(vh) + a.eps);
+        } else {
+          theta[p] = fma(-lr, g, theta[p]);
+        }
+      }
     }
     if (tid == 0) {
       if (gd && a.etraj) {

@@ -99,6 +99,13 @@ struct BatchArgs {
   const double* lr_inst;   // per-instance steps, or nullptr
   double* etraj;           // energies before each update ([n_steps x n_inst], or per
                            // instance at BInst::etraj_off when n_steps < 0), or nullptr
+  // Optimizer of the update step: 0 gradient descent; 1 Adam with first/second moments
+  // adam_m/adam_v (indexed like grad) and t0 updates already taken.
+  int opt;
+  double* adam_m;
+  double* adam_v;
+  int adam_t0;
+  double beta1, beta2, eps;
 };
 
 // Threads per CTA of the batched kernel and its dynamic shared memory for nmax qubits.

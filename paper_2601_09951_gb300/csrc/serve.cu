@@ -461,6 +461,12 @@ void worker_loop(sv_server* s) {
         a.lr = 0.0;
         a.lr_inst = nullptr;
         a.etraj = (double*)s->arena;
+        a.opt = 0;
+        a.adam_m = a.adam_v = nullptr;
+        a.adam_t0 = 0;
+        a.beta1 = 0.9;
+        a.beta2 = 0.999;
+        a.eps = 1e-8;
         cudaError_t e;
         if ((e = cudaMemcpyAsync(s->d_inst, s->h_inst, bi.size() * sizeof(BInst),
                                  cudaMemcpyHostToDevice, s->bstream)) != cudaSuccess ||

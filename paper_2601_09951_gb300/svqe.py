@@ -93,6 +93,7 @@ def lib():
         "sv_batch_run": ([P, P, P, P], i32),
         "sv_batch_run_dev": ([P, P, P, P], i32),
         "sv_batch_vqe_dev": ([P, P, dbl, i32, P], i32),
+        "sv_batch_adam_dev": ([P, P, dbl, i32, P, i32], i32),
         "sv_adjoint_grad_noalloc": ([P, u64, P, i32, P, P, P, P, P], i32),
         "sv_server_create": ([P, P], i32),
         "sv_server_submit": ([P, P, P, i32, dbl, P], i32),
@@ -107,6 +108,17 @@ def lib():
         fn.restype = res
     _lib = L
     return L
+
+
+_LEGACY_STREAM = 1  # cudaStreamLegacy: torch reports its default stream as handle 0
+
+
+def _stream_arg(stream):
+    """None: the library creates its own stream; an int handle (0 = torch's default stream,
+    passed on as cudaStreamLegacy) otherwise."""
+    if stream is None:
+        return None
+    return ctypes.c_void_p(int(stream) if int(stream) != 0 else _LEGACY_STREAM)
 
 
 def _check(status):
@@ -210,7 +222,7 @@ def adjoint_grad_noalloc(circuit, ref, groups_ptr, n_groups, tables_ptr, theta_p
     _check(lib().sv_adjoint_grad_noalloc(
         C.ref(), int(ref), ctypes.c_void_p(groups_ptr), int(n_groups),
         ctypes.c_void_p(tables_ptr), ctypes.c_void_p(theta_ptr), ctypes.c_void_p(energy_ptr),
-        ctypes.c_void_p(grad_ptr), ctypes.c_void_p(stream) if stream else None))
+        ctypes.c_void_p(grad_ptr), _stream_arg(stream)))
 
 
 class Ham:
@@ -249,8 +261,7 @@ class Context:
     def __init__(self, n, stream=None):
         self._c = ctypes.c_void_p()
         self.n = int(n)
-        _check(lib().sv_create(ctypes.byref(self._c), self.n,
-                               ctypes.c_void_p(stream) if stream else None))
+        _check(lib().sv_create(ctypes.byref(self._c), self.n, _stream_arg(stream)))
 
     @property
     def handle(self):
@@ -337,8 +348,7 @@ class Batch:
             arr[i].ref = int(inst["ref"])
             offs.append(offs[-1] + C.n_params)
         self.offsets = np.array(offs, dtype=np.int64)
-        _check(lib().sv_batch_create(arr, len(instances),
-                                     ctypes.c_void_p(stream) if stream else None,
+        _check(lib().sv_batch_create(arr, len(instances), _stream_arg(stream),
                                      ctypes.byref(self._b)))
         self._keep = None
         ni, npar = ctypes.c_int32(), ctypes.c_int64()
@@ -376,6 +386,12 @@ class Batch:
         _check(lib().sv_batch_vqe_dev(self._b, ctypes.c_void_p(theta_ptr), float(lr),
                                       int(n_steps),
                                       ctypes.c_void_p(etraj_ptr) if etraj_ptr else None))
+
+    def adam_dev(self, theta_ptr, lr, n_steps, etraj_ptr=None, reset=True):
+        _check(lib().sv_batch_adam_dev(self._b, ctypes.c_void_p(theta_ptr), float(lr),
+                                       int(n_steps),
+                                       ctypes.c_void_p(etraj_ptr) if etraj_ptr else None,
+                                       1 if reset else 0))
 
     def close(self):
         if self._b:

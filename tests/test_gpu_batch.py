@@ -108,3 +108,29 @@ def test_cost_model_counts_by_hand():
     b = svqe.Batch(W.h2_sweep(1))
     flops, _ = b.cost()
     assert flops == 44 + 2 * 16 * 4 + 16 * 4
+
+
+def test_on_device_adam_h2_sweep_paper_settings():
+    """The paper's procedure (Sec. 3.4): Adam with alpha = 0.01 from theta = 0, 200 iterations,
+    over 100 bond lengths in one launch; per-step energies against the oracle's Adam on
+    sampled bonds, and the same trajectory when run one step per call (moments persist)."""
+    torch = pytest.importorskip("torch")
+    insts = W.h2_sweep(100)
+    b = svqe.Batch(insts)
+    T = 200
+    th = torch.zeros(100, dtype=torch.float64, device="cuda")
+    traj = torch.empty(T, 100, dtype=torch.float64, device="cuda")
+    b.adam_dev(th.data_ptr(), 0.01, T, traj.data_ptr(), reset=True)
+    torch.cuda.synchronize()
+    traj = traj.cpu().numpy()
+    for i in (0, 37, 74, 99):
+        es, _, th_end = oracle.adam_trajectory(insts[i], 0.01, T)
+        for t in range(T):
+            assert_energy(traj[t, i], es[t], insts[i]["ham"], f"bond {i} step {t}")
+        assert abs(th.cpu().numpy()[i] - th_end[0]) <= 1e-9
+    th1 = torch.zeros(100, dtype=torch.float64, device="cuda")
+    b.adam_dev(th1.data_ptr(), 0.01, 1, None, reset=True)
+    for _ in range(T - 1):
+        b.adam_dev(th1.data_ptr(), 0.01, 1, None, reset=False)
+    torch.cuda.synchronize()
+    assert np.array_equal(th1.cpu().numpy(), th.cpu().numpy())

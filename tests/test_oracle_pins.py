@@ -314,3 +314,17 @@ def test_gradient_subset_equals_full_sweep_entries():
     assert es == e
     for p, v in gs.items():
         assert v == g[p]
+
+
+def test_adam_first_step_and_scale_invariance():
+    """Adam's first update is lr * g / (|g| + eps) per parameter (m_hat = g, v_hat = g^2),
+    and scaling H (hence g) by a constant leaves the trajectory unchanged up to eps."""
+    inst = W.hea_instance(5, 2, 30, 61)
+    es, ths, _ = oracle.adam_trajectory(inst, 0.01, 3)
+    _, g = oracle.energy_grad(inst)
+    step1 = ths[1] - ths[0] if len(ths) > 1 else None
+    np.testing.assert_allclose(step1, -0.01 * g / (np.abs(g) + 1e-8), rtol=1e-12, atol=1e-15)
+    big = dict(inst, ham=dict(inst["ham"], coeff=10.0 * inst["ham"]["coeff"]))
+    es10, ths10, _ = oracle.adam_trajectory(big, 0.01, 3)
+    np.testing.assert_allclose(ths10, ths, atol=1e-7)
+    np.testing.assert_allclose(es10, 10 * es, rtol=1e-6, atol=1e-9)
