@@ -206,6 +206,22 @@ __device__ __forceinline__ void op_pass(const Team& T, double2* v, uint32_t N, c
   }
 }
 
+// Copy N amplitudes between the team's shared buffer and its checkpoint, four loads in flight
+// per thread before the stores.
+__device__ __forceinline__ void team_copy(const Team& T, double2* dst, const double2* src,
+                                          uint32_t N) {
+  const uint32_t s = T.size;
+  uint32_t k = T.rank;
+  for (; k + 3 * s < N; k += 4 * s) {
+    const double2 a = src[k], b = src[k + s], c = src[k + 2 * s], d = src[k + 3 * s];
+    dst[k] = a;
+    dst[k + s] = b;
+    dst[k + 2 * s] = c;
+    dst[k + 3 * s] = d;
+  }
+  for (; k < N; k += s) dst[k] = src[k];
+}
+
 // Apply two single-qubit ops on distinct bits in one pass: each thread takes the four
 // amplitudes of a block (both bits 0, either, both 1), rotates them for the first op, then for
 // the second, in registers.  Half the barriers and shared-memory traffic of two op_pass calls.
@@ -324,8 +340,7 @@ __device__ void run_instance(const BatchArgs& a, int idx, const Team& T, TeamS& 
     for (int s = 0; s < I.n_segs; ++s) {
       const Seg sg = segs[s];
       if (sg.ckpt >= 0) {
-        double2* dst = ck + (size_t)sg.ckpt * N;
-        for (uint32_t k = tid; k < N; k += TS) dst[k] = psi[k];
+        team_copy(T, ck + (size_t)sg.ckpt * N, psi, N);
         T.sync();
       }
       if (sg.kind == SEG_PERM) {
@@ -470,8 +485,7 @@ __device__ void run_instance(const BatchArgs& a, int idx, const Team& T, TeamS& 
         double2* t = psi;
         psi = lam;
         lam = t;
-        const double2* src = ck + (size_t)sg.ckpt * N;
-        for (uint32_t k = tid; k < N; k += TS) psi[k] = src[k];
+        team_copy(T, psi, ck + (size_t)sg.ckpt * N, N);
         T.sync();
         continue;
       }
@@ -564,8 +578,7 @@ __device__ void run_instance(const BatchArgs& a, int idx, const Team& T, TeamS& 
         if (tid < m) contrib[S.rz_op[tid]] = tot;
       }
       // psi before the segment, from the forward pass's checkpoint
-      const double2* src = ck + (size_t)sg.ckpt * N;
-      for (uint32_t k = tid; k < N; k += TS) psi[k] = src[k];
+      team_copy(T, psi, ck + (size_t)sg.ckpt * N, N);
       T.sync();
     }
 

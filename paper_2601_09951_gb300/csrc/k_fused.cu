@@ -108,151 +108,24 @@ __device__ void setup_hoff(uint64_t* hoff, const FPass& P) {
   for (int j = threadIdx.x; j < (1 << (P.m - P.c)); j += blockDim.x) hoff[j] = pdep64(j, hm);
 }
 
-enum FKind { F_SWAP = 0, F_H = 1, F_ROTY = 2, F_ROTX = 3, F_ROTZ = 4, F_NEG = 5 };
-
-__device__ __forceinline__ int fkind_of(int type) {
-  switch (type) {
-    case SV_GATE_H: return F_H;
-    case SV_GATE_RY: case SV_GATE_SINGLE_EXC: case SV_GATE_DOUBLE_EXC: return F_ROTY;
-    case SV_GATE_RX: return F_ROTX;
-    case SV_GATE_RZ: return F_ROTZ;
-    case SV_GATE_CZ: return F_NEG;
-    default: return F_SWAP;
-  }
-}
-
-// One pair of one kind, rotation coefficients already oriented (inverse taken by the caller).
-template <int KIND>
-__device__ __forceinline__ void fapply(const Rot& r, double2& x, double2& y) {
-  if (KIND == F_SWAP) {
-    const double2 t = x; x = y; y = t;
-  } else if (KIND == F_H) {
-    pair_apply(SV_GATE_H, r, false, x, y);
-  } else if (KIND == F_ROTY) {
-    rot_apply(r, x.x, y.x);
-    rot_apply(r, x.y, y.y);
-  } else if (KIND == F_ROTX) {
-    const Rot m = rot_inverse(r);
-    rot_apply(m, x.x, y.y);
-    rot_apply(r, x.y, y.x);
-  } else if (KIND == F_ROTZ) {
-    const Rot m = rot_inverse(r);
-    rot_apply(m, x.x, x.y);
-    rot_apply(r, y.x, y.y);
-  }
-}
-
-// acc += 2 Im<lambda|G|psi> on one pair, folded into FMAs.
-template <int KIND>
-__device__ __forceinline__ void fgrad(const double2& lx, const double2& ly, const double2& px,
-                                      const double2& py, double& acc) {
-  if (KIND == F_ROTX) {
-    acc = fma(lx.x, py.y, acc);
-    acc = fma(dneg(lx.y), py.x, acc);
-    acc = fma(ly.x, px.y, acc);
-    acc = fma(dneg(ly.y), px.x, acc);
-  } else if (KIND == F_ROTZ) {
-    acc = fma(lx.x, px.y, acc);
-    acc = fma(dneg(lx.y), px.x, acc);
-    acc = fma(dneg(ly.x), py.y, acc);
-    acc = fma(ly.y, py.x, acc);
-  } else if (KIND == F_ROTY) {
-    acc = fma(ly.x, px.x, acc);
-    acc = fma(ly.y, px.y, acc);
-    acc = fma(dneg(lx.x), py.x, acc);
-    acc = fma(dneg(lx.y), py.y, acc);
-  }
-}
-
-// Apply one op to a tile, two pairs per iteration (both loaded before either is stored).
-template <int KIND>
-__device__ __forceinline__ void tile_op_k(double2* v, uint32_t M, const DOp& op, const Rot& r) {
-  const uint32_t np = M >> op.k;
-  const uint32_t lo = (uint32_t)op.lo_or, fl = (uint32_t)op.flip;
-  if (KIND == F_NEG) {
-    for (uint32_t p = threadIdx.x; p < np; p += kFT) {
-      const uint32_t i = (uint32_t)insert_zeros(p, op.sb, op.k) | lo;
-      v[i] = make_double2(dneg(v[i].x), dneg(v[i].y));
-    }
-    return;
-  }
-  for (uint32_t p = threadIdx.x; p < np; p += 2 * kFT) {
-    const uint32_t p2 = p + kFT;
-    const bool two = p2 < np;
-    const uint32_t i = (uint32_t)insert_zeros(p, op.sb, op.k) | lo;
-    const uint32_t i2 = (uint32_t)insert_zeros(p2, op.sb, op.k) | lo;
-    double2 x = v[i], y = v[i ^ fl], x2, y2;
-    if (two) {
-      x2 = v[i2];
-      y2 = v[i2 ^ fl];
-    }
-    fapply<KIND>(r, x, y);
-    if (two) fapply<KIND>(r, x2, y2);
-    v[i] = x;
-    v[i ^ fl] = y;
-    if (two) {
-      v[i2] = x2;
-      v[i2 ^ fl] = y2;
-    }
-  }
-}
-
-__device__ __forceinline__ void tile_op(double2* v, uint32_t M, const DOp& op, const Rot& rf,
+__device__ __forceinline__ void tile_op(double2* v, uint32_t M, const DOp& op, const Rot& r,
                                         bool inv) {
-  const Rot r = inv ? rot_inverse(rf) : rf;
-  switch (fkind_of(op.type)) {
-    case F_SWAP: tile_op_k<F_SWAP>(v, M, op, r); break;
-    case F_H: tile_op_k<F_H>(v, M, op, r); break;
-    case F_ROTY: tile_op_k<F_ROTY>(v, M, op, r); break;
-    case F_ROTX: tile_op_k<F_ROTX>(v, M, op, r); break;
-    case F_ROTZ: tile_op_k<F_ROTZ>(v, M, op, r); break;
-    default: tile_op_k<F_NEG>(v, M, op, r); break;
-  }
-}
-
-// Adjoint step of one op on the psi and lambda tiles: gradient share into acc (if grad), then
-// un-apply to both, two pairs per iteration.
-template <int KIND>
-__device__ __forceinline__ void tile_adj_k(double2* tp, double2* tl, uint32_t M, const DOp& op,
-                                           const Rot& ri, bool grad, double& acc) {
   const uint32_t np = M >> op.k;
-  const uint32_t lo = (uint32_t)op.lo_or, fl = (uint32_t)op.flip;
-  if (KIND == F_NEG) {
-    for (uint32_t p = threadIdx.x; p < np; p += kFT) {
-      const uint32_t a = (uint32_t)insert_zeros(p, op.sb, op.k) | lo;
-      tp[a] = make_double2(dneg(tp[a].x), dneg(tp[a].y));
-      tl[a] = make_double2(dneg(tl[a].x), dneg(tl[a].y));
-    }
-    return;
-  }
-  double acc2 = 0.0;
-  for (uint32_t p = threadIdx.x; p < np; p += 2 * kFT) {
-    const uint32_t p2 = p + kFT;
-    const bool two = p2 < np;
-    const uint32_t a = (uint32_t)insert_zeros(p, op.sb, op.k) | lo;
-    const uint32_t a2 = (uint32_t)insert_zeros(p2, op.sb, op.k) | lo;
-    double2 px = tp[a], py = tp[a ^ fl], lx = tl[a], ly = tl[a ^ fl];
-    double2 px2, py2, lx2, ly2;
-    if (two) {
-      px2 = tp[a2]; py2 = tp[a2 ^ fl]; lx2 = tl[a2]; ly2 = tl[a2 ^ fl];
-    }
-    if (grad) fgrad<KIND>(lx, ly, px, py, acc);
-    if (grad && two) fgrad<KIND>(lx2, ly2, px2, py2, acc2);
-    fapply<KIND>(ri, px, py);
-    fapply<KIND>(ri, lx, ly);
-    if (two) {
-      fapply<KIND>(ri, px2, py2);
-      fapply<KIND>(ri, lx2, ly2);
-    }
-    tp[a] = px; tp[a ^ fl] = py; tl[a] = lx; tl[a ^ fl] = ly;
-    if (two) {
-      tp[a2] = px2; tp[a2 ^ fl] = py2; tl[a2] = lx2; tl[a2 ^ fl] = ly2;
+  for (uint32_t p = threadIdx.x; p < np; p += kFT) {
+    const uint32_t i = (uint32_t)insert_zeros(p, op.sb, op.k) | (uint32_t)op.lo_or;
+    if (op.type == SV_GATE_CZ) {
+      v[i] = make_double2(dneg(v[i].x), dneg(v[i].y));
+    } else {
+      const uint32_t j = i ^ (uint32_t)op.flip;
+      double2 x = v[i], y = v[j];
+      pair_apply(op.type, r, inv, x, y);
+      v[i] = x;
+      v[j] = y;
     }
   }
-  acc += acc2;
 }
 
-__global__ void __launch_bounds__(kFT, 4) k_fpass(double2* __restrict__ psi, FPass P,
+__global__ void __launch_bounds__(kFT) k_fpass(double2* __restrict__ psi, FPass P,
                                                const FItem* __restrict__ items,
                                                const DOp* __restrict__ gops,
                                                const Rot* __restrict__ coef,
@@ -287,7 +160,7 @@ __global__ void __launch_bounds__(kFT, 4) k_fpass(double2* __restrict__ psi, FPa
   }
 }
 
-__global__ void __launch_bounds__(kFT, 2) k_bpass(double2* __restrict__ psi,
+__global__ void __launch_bounds__(kFT) k_bpass(double2* __restrict__ psi,
                                                double2* __restrict__ lam, FPass P,
                                                const FItem* __restrict__ items,
                                                const DOp* __restrict__ gops,
@@ -324,18 +197,27 @@ __global__ void __launch_bounds__(kFT, 2) k_bpass(double2* __restrict__ psi,
       const FItem it = items[P.first_item + i];
       if (it.kind == 0) {
         const DOp& op = it.local;
-        const Rot ri = rot_inverse(coef[it.op]);
-        const bool gr = it.slot >= 0;
+        const Rot r = coef[it.op];
+        const uint32_t np = M >> op.k;
         double acc = 0.0;
-        switch (fkind_of(op.type)) {
-          case F_SWAP: tile_adj_k<F_SWAP>(tp, tlam, M, op, ri, false, acc); break;
-          case F_H: tile_adj_k<F_H>(tp, tlam, M, op, ri, false, acc); break;
-          case F_ROTY: tile_adj_k<F_ROTY>(tp, tlam, M, op, ri, gr, acc); break;
-          case F_ROTX: tile_adj_k<F_ROTX>(tp, tlam, M, op, ri, gr, acc); break;
-          case F_ROTZ: tile_adj_k<F_ROTZ>(tp, tlam, M, op, ri, gr, acc); break;
-          default: tile_adj_k<F_NEG>(tp, tlam, M, op, ri, false, acc); break;
+        for (uint32_t p = tid; p < np; p += kFT) {
+          const uint32_t a = (uint32_t)insert_zeros(p, op.sb, op.k) | (uint32_t)op.lo_or;
+          if (op.type == SV_GATE_CZ) {
+            tp[a] = make_double2(dneg(tp[a].x), dneg(tp[a].y));
+            tlam[a] = make_double2(dneg(tlam[a].x), dneg(tlam[a].y));
+          } else {
+            const uint32_t b = a ^ (uint32_t)op.flip;
+            double2 px = tp[a], py = tp[b], lx = tlam[a], ly = tlam[b];
+            if (it.slot >= 0) acc += pair_grad(op.type, lx, ly, px, py);
+            pair_apply(op.type, r, true, px, py);
+            pair_apply(op.type, r, true, lx, ly);
+            tp[a] = px;
+            tp[b] = py;
+            tlam[a] = lx;
+            tlam[b] = ly;
+          }
         }
-        if (gr) accp[it.slot * kFT + tid] += acc;
+        if (it.slot >= 0) accp[it.slot * kFT + tid] += acc;
       } else {
         // gradients of the RZ gates: 2 Im<lambda|Z_q/2|psi> = sum_k s_q(k) Im(conj(l_k) p_k)
         double W = 0.0;
