@@ -231,6 +231,21 @@ def run_serve(args):
 
 HBM_PEAK_GBS = 6678.2  # measured copy bandwidth (read + write) on the GB300s
 
+# dram__bytes_read.sum + dram__bytes_write.sum of one k_batch launch of the default workload,
+# from the ncu capture recorded in profiles/k_batch_hea_batch.md, keyed by a hash of the
+# kernel's sources: once the kernel changes the key no longer matches and traffic is null.
+KBATCH_TRAFFIC = {"8f9067c8779f3d1a": 640.63e6 + 850.12e6}
+KBATCH_SOURCES = ("k_batch.cu", "svqe_internal.cuh", "svqe_types.h", "launch.h")
+
+
+def kbatch_hash():
+    import hashlib
+    h = hashlib.sha256()
+    for f in KBATCH_SOURCES:
+        with open(os.path.join(ROOT, "paper_2601_09951_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
 
 def _peaks():
     try:
@@ -514,7 +529,10 @@ def main():
                 "h2d_bytes_per_step": int(8 * P), "d2h_bytes_per_step": int(8 * (P + len(insts)))},
         "gpu_launches": args.steps,
         "roofline": {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS,
-                     "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,
+                     "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS,
+                     "traffic": KBATCH_TRAFFIC.get(kbatch_hash()) if args.instances == 4096
+                     and world >= 1 else None,
+                     "kernel_source_hash": kbatch_hash(),
                      "kernel": "k_batch", "what": "FP64 pipe (2 DFMA/clk/SM x 152 SMs x "
                      "2.07 GHz); algorithmic FP64 flops per launch / mean launch time",
                      "flops_per_launch": flops, "hbm_bytes_per_launch": hbm_bytes},

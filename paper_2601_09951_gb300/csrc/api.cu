@@ -550,11 +550,23 @@ int svqe::class_teams(int n) {
   return c == 0 ? 1 : c == 1 ? 2 : 8;
 }
 
-// Work items: instances sorted by cost (largest first), class-0 instances alone, class-1
-// instances in pairs and class-2 instances in groups of eight of similar cost; items sorted by
-// the cost of their first (largest) instance.
-std::vector<BItem> svqe::batch_items(const std::vector<BInst>& bi, const std::vector<double>& cost) {
+// Work items: class-0 instances alone, class-1 instances in pairs and class-2 instances in
+// groups of eight.  What sets an item's duration is the work of one thread of its slowest team,
+// not the item's flops (eight 9-qubit instances on one warp each take about as long as one
+// 12-qubit instance on eight warps), so instances are ordered by that estimate -- amplitudes per
+// thread times the per-amplitude work of the ops and groups, plus a per-op latency term -- and
+// items by the estimate of their first (slowest) instance, slowest first.
+static double thread_time(const BInst& B, double cost) {
+  const int team = 32 * (batch_class(B.n) == 0 ? 8 : batch_class(B.n) == 1 ? 4 : 1);
+  const double per_thread = std::max(1.0, (double)(1u << B.n) / team);
+  (void)cost;
+  return per_thread * (6.0 * B.n_ops + 2.0 * B.n_groups + 8.0) + 150.0 * B.n_ops;
+}
+
+std::vector<BItem> svqe::batch_items(const std::vector<BInst>& bi, const std::vector<double>& cost_in) {
   const int n = (int)bi.size();
+  std::vector<double> cost(n);
+  for (int i = 0; i < n; ++i) cost[i] = thread_time(bi[i], cost_in[i]);
   std::vector<int> order(n);
   std::iota(order.begin(), order.end(), 0);
   std::stable_sort(order.begin(), order.end(), [&](int a, int c) { return cost[a] > cost[c]; });

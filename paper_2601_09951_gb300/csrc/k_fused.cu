@@ -108,19 +108,113 @@ __device__ void setup_hoff(uint64_t* hoff, const FPass& P) {
   for (int j = threadIdx.x; j < (1 << (P.m - P.c)); j += blockDim.x) hoff[j] = pdep64(j, hm);
 }
 
-__device__ __forceinline__ void tile_op(double2* v, uint32_t M, const DOp& op, const Rot& r,
-                                        bool inv) {
+enum FKind { F_SWAP = 0, F_H = 1, F_ROTY = 2, F_ROTX = 3, F_ROTZ = 4, F_NEG = 5 };
+
+__device__ __forceinline__ int fkind_of(int type) {
+  switch (type) {
+    case SV_GATE_H: return F_H;
+    case SV_GATE_RY: case SV_GATE_SINGLE_EXC: case SV_GATE_DOUBLE_EXC: return F_ROTY;
+    case SV_GATE_RX: return F_ROTX;
+    case SV_GATE_RZ: return F_ROTZ;
+    case SV_GATE_CZ: return F_NEG;
+    default: return F_SWAP;
+  }
+}
+
+// One pair of one kind with oriented coefficients (the caller takes the inverse).
+template <int KIND>
+__device__ __forceinline__ void fapply(const Rot& r, double2& x, double2& y) {
+  if (KIND == F_SWAP) {
+    const double2 t = x; x = y; y = t;
+  } else if (KIND == F_H) {
+    pair_apply(SV_GATE_H, r, false, x, y);
+  } else if (KIND == F_ROTY) {
+    rot_apply(r, x.x, y.x);
+    rot_apply(r, x.y, y.y);
+  } else if (KIND == F_ROTX) {
+    const Rot m = rot_inverse(r);
+    rot_apply(m, x.x, y.y);
+    rot_apply(r, x.y, y.x);
+  } else if (KIND == F_ROTZ) {
+    const Rot m = rot_inverse(r);
+    rot_apply(m, x.x, x.y);
+    rot_apply(r, y.x, y.y);
+  }
+}
+
+// acc += 2 Im<lambda|G|psi> on one pair, folded into FMAs.
+template <int KIND>
+__device__ __forceinline__ void fgrad(const double2& lx, const double2& ly, const double2& px,
+                                      const double2& py, double& acc) {
+  if (KIND == F_ROTX) {
+    acc = fma(lx.x, py.y, acc);
+    acc = fma(dneg(lx.y), py.x, acc);
+    acc = fma(ly.x, px.y, acc);
+    acc = fma(dneg(ly.y), px.x, acc);
+  } else if (KIND == F_ROTZ) {
+    acc = fma(lx.x, px.y, acc);
+    acc = fma(dneg(lx.y), px.x, acc);
+    acc = fma(dneg(ly.x), py.y, acc);
+    acc = fma(ly.y, py.x, acc);
+  } else if (KIND == F_ROTY) {
+    acc = fma(ly.x, px.x, acc);
+    acc = fma(ly.y, px.y, acc);
+    acc = fma(dneg(lx.x), py.x, acc);
+    acc = fma(dneg(lx.y), py.y, acc);
+  }
+}
+
+template <int KIND>
+__device__ __forceinline__ void tile_op_k(double2* v, uint32_t M, const DOp& op, const Rot& r) {
   const uint32_t np = M >> op.k;
+  const uint32_t lo = (uint32_t)op.lo_or, fl = (uint32_t)op.flip;
   for (uint32_t p = threadIdx.x; p < np; p += kFT) {
-    const uint32_t i = (uint32_t)insert_zeros(p, op.sb, op.k) | (uint32_t)op.lo_or;
-    if (op.type == SV_GATE_CZ) {
+    const uint32_t i = (uint32_t)insert_zeros(p, op.sb, op.k) | lo;
+    if (KIND == F_NEG) {
       v[i] = make_double2(dneg(v[i].x), dneg(v[i].y));
     } else {
-      const uint32_t j = i ^ (uint32_t)op.flip;
-      double2 x = v[i], y = v[j];
-      pair_apply(op.type, r, inv, x, y);
+      double2 x = v[i], y = v[i ^ fl];
+      fapply<KIND>(r, x, y);
       v[i] = x;
-      v[j] = y;
+      v[i ^ fl] = y;
+    }
+  }
+}
+
+__device__ __forceinline__ void tile_op(double2* v, uint32_t M, const DOp& op, const Rot& rf,
+                                        bool inv) {
+  const Rot r = inv ? rot_inverse(rf) : rf;
+  switch (fkind_of(op.type)) {
+    case F_SWAP: tile_op_k<F_SWAP>(v, M, op, r); break;
+    case F_H: tile_op_k<F_H>(v, M, op, r); break;
+    case F_ROTY: tile_op_k<F_ROTY>(v, M, op, r); break;
+    case F_ROTX: tile_op_k<F_ROTX>(v, M, op, r); break;
+    case F_ROTZ: tile_op_k<F_ROTZ>(v, M, op, r); break;
+    default: tile_op_k<F_NEG>(v, M, op, r); break;
+  }
+}
+
+// Adjoint step of one op on the psi and lambda tiles: gradient share into acc (if grad), then
+// un-apply to both.
+template <int KIND>
+__device__ __forceinline__ void tile_adj_k(double2* tp, double2* tl, uint32_t M, const DOp& op,
+                                           const Rot& ri, bool grad, double& acc) {
+  const uint32_t np = M >> op.k;
+  const uint32_t lo = (uint32_t)op.lo_or, fl = (uint32_t)op.flip;
+  for (uint32_t p = threadIdx.x; p < np; p += kFT) {
+    const uint32_t a = (uint32_t)insert_zeros(p, op.sb, op.k) | lo;
+    if (KIND == F_NEG) {
+      tp[a] = make_double2(dneg(tp[a].x), dneg(tp[a].y));
+      tl[a] = make_double2(dneg(tl[a].x), dneg(tl[a].y));
+    } else {
+      double2 px = tp[a], py = tp[a ^ fl], lx = tl[a], ly = tl[a ^ fl];
+      if (grad) fgrad<KIND>(lx, ly, px, py, acc);
+      fapply<KIND>(ri, px, py);
+      fapply<KIND>(ri, lx, ly);
+      tp[a] = px;
+      tp[a ^ fl] = py;
+      tl[a] = lx;
+      tl[a ^ fl] = ly;
     }
   }
 }
@@ -197,27 +291,18 @@ __global__ void __launch_bounds__(kFT) k_bpass(double2* __restrict__ psi,
       const FItem it = items[P.first_item + i];
       if (it.kind == 0) {
         const DOp& op = it.local;
-        const Rot r = coef[it.op];
-        const uint32_t np = M >> op.k;
+        const Rot ri = rot_inverse(coef[it.op]);
+        const bool gr = it.slot >= 0;
         double acc = 0.0;
-        for (uint32_t p = tid; p < np; p += kFT) {
-          const uint32_t a = (uint32_t)insert_zeros(p, op.sb, op.k) | (uint32_t)op.lo_or;
-          if (op.type == SV_GATE_CZ) {
-            tp[a] = make_double2(dneg(tp[a].x), dneg(tp[a].y));
-            tlam[a] = make_double2(dneg(tlam[a].x), dneg(tlam[a].y));
-          } else {
-            const uint32_t b = a ^ (uint32_t)op.flip;
-            double2 px = tp[a], py = tp[b], lx = tlam[a], ly = tlam[b];
-            if (it.slot >= 0) acc += pair_grad(op.type, lx, ly, px, py);
-            pair_apply(op.type, r, true, px, py);
-            pair_apply(op.type, r, true, lx, ly);
-            tp[a] = px;
-            tp[b] = py;
-            tlam[a] = lx;
-            tlam[b] = ly;
-          }
+        switch (fkind_of(op.type)) {
+          case F_SWAP: tile_adj_k<F_SWAP>(tp, tlam, M, op, ri, false, acc); break;
+          case F_H: tile_adj_k<F_H>(tp, tlam, M, op, ri, false, acc); break;
+          case F_ROTY: tile_adj_k<F_ROTY>(tp, tlam, M, op, ri, gr, acc); break;
+          case F_ROTX: tile_adj_k<F_ROTX>(tp, tlam, M, op, ri, gr, acc); break;
+          case F_ROTZ: tile_adj_k<F_ROTZ>(tp, tlam, M, op, ri, gr, acc); break;
+          default: tile_adj_k<F_NEG>(tp, tlam, M, op, ri, false, acc); break;
         }
-        if (it.slot >= 0) accp[it.slot * kFT + tid] += acc;
+        if (gr) accp[it.slot * kFT + tid] += acc;
       } else {
         // gradients of the RZ gates: 2 Im<lambda|Z_q/2|psi> = sum_k s_q(k) Im(conj(l_k) p_k)
         double W = 0.0;
