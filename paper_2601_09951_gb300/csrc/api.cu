@@ -606,8 +606,8 @@ std::vector<BItem> svqe::batch_items(const std::vector<BInst>& bi, const std::ve
 
 // FP64 flops (FMA = 2) of one instance's forward pass, lambda = H psi and adjoint sweep, as
 // k_batch executes its segments: lifting rotation 12 per pair, gradient 8 per pair, H gate 8
-// per pair; a diagonal segment 12 per amplitude forward and 16 + (RZ gates on bits >= 8)
-// backward; a commuting layer un-applies lambda only; groups 4 (real or imaginary table) or 8
+// per pair; a diagonal segment (alone or fused with the permutation after it) 12 per
+// amplitude forward and 16 + (RZ gates on bits >= 8) backward; a commuting layer un-applies lambda only; groups 4 (real or imaginary table) or 8
 // (complex) per amplitude plus 4 for the energy.
 double svqe::batch_instance_flops(const HostCircuit& hc, const HostHam& hh,
                             const std::vector<Seg>& segs) {
@@ -625,7 +625,7 @@ double svqe::batch_instance_flops(const HostCircuit& hc, const HostHam& hh,
         f += pairs * (12 + 8 + 12);
       }
     }
-    if (s.kind == SEG_DIAG) {
+    if (s.kind == SEG_DIAG || s.kind == SEG_DIAGPERM) {
       int hi = 0;
       for (int l = s.first; l < s.first + s.count; ++l)
         if (hc.ops[l].type == SV_GATE_RZ && hc.ops[l].bit0 >= 8) ++hi;

@@ -135,20 +135,22 @@ int segment_ops(const std::vector<DOp>& ops, int min_layer, int min_diag_rz,
         segs.back().first + segs.back().count == first) {
       segs.back().count += count;
     } else {
-      segs.push_back(Seg{SEG_GATES, first, count, -1});
+      segs.push_back(Seg{SEG_GATES, 0, first, count, -1});
     }
   };
   int l = 0;
   while (l < n_ops) {
     const int t = ops[l].type;
     if (t == SV_GATE_RZ || t == SV_GATE_CZ) {
-      int e = l, n_rz = 0;
+      int e = l, n_rz = 0, n_cz = 0;
       while (e < n_ops && (ops[e].type == SV_GATE_RZ || ops[e].type == SV_GATE_CZ) &&
-             n_rz + (ops[e].type == SV_GATE_RZ) <= kMaxLayer) {
+             n_rz + (ops[e].type == SV_GATE_RZ) <= kMaxLayer &&
+             n_cz + (ops[e].type == SV_GATE_CZ) <= kMaxLayer) {
         n_rz += ops[e].type == SV_GATE_RZ;
+        n_cz += ops[e].type == SV_GATE_CZ;
         ++e;
       }
-      if (n_rz >= min_diag_rz) segs.push_back(Seg{SEG_DIAG, l, e - l, ckpt++});
+      if (n_rz >= min_diag_rz) segs.push_back(Seg{SEG_DIAG, 0, l, e - l, ckpt++});
       else push_gates(l, e - l);
       l = e;
     } else if (t == SV_GATE_RY || t == SV_GATE_RX) {
@@ -159,7 +161,7 @@ int segment_ops(const std::vector<DOp>& ops, int min_layer, int min_diag_rz,
         used |= 1ull << ops[e].bit0;
         ++e;
       }
-      if (e - l >= min_layer) segs.push_back(Seg{SEG_RLAYER, l, e - l, ckpt++});
+      if (e - l >= min_layer) segs.push_back(Seg{SEG_RLAYER, 0, l, e - l, ckpt++});
       else push_gates(l, e - l);
       l = e;
     } else if (t == SV_GATE_CNOT || t == SV_GATE_X) {
@@ -167,7 +169,7 @@ int segment_ops(const std::vector<DOp>& ops, int min_layer, int min_diag_rz,
       while (e < n_ops && (ops[e].type == SV_GATE_CNOT || ops[e].type == SV_GATE_X) &&
              e - l < kMaxPerm)
         ++e;
-      if (e - l >= 2) segs.push_back(Seg{SEG_PERM, l, e - l, ckpt++});
+      if (e - l >= 2) segs.push_back(Seg{SEG_PERM, 0, l, e - l, ckpt++});
       else push_gates(l, e - l);
       l = e;
     } else {
@@ -180,6 +182,22 @@ int segment_ops(const std::vector<DOp>& ops, int min_layer, int min_diag_rz,
       l = e;
     }
   }
+  // A diagonal segment directly followed by a permutation segment becomes one SEG_DIAGPERM
+  // with a single checkpoint (psi before the phase); checkpoints are then renumbered in order.
+  std::vector<Seg> merged;
+  for (size_t s = 0; s < segs.size(); ++s) {
+    if (segs[s].kind == SEG_DIAG && s + 1 < segs.size() && segs[s + 1].kind == SEG_PERM &&
+        segs[s + 1].first == segs[s].first + segs[s].count) {
+      merged.push_back(Seg{SEG_DIAGPERM, (int16_t)segs[s].count, segs[s].first,
+                           segs[s].count + segs[s + 1].count, 0});
+      ++s;
+    } else {
+      merged.push_back(segs[s]);
+    }
+  }
+  ckpt = 0;
+  for (Seg& s : merged) s.ckpt = s.kind == SEG_GATES ? -1 : ckpt++;
+  segs.swap(merged);
   return ckpt;
 }
 

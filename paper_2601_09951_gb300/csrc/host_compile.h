@@ -33,10 +33,11 @@ struct HostCircuit {
 sv_status lower_circuit(const sv_circuit* c, int expect_n, HostCircuit& out);
 
 // Split a lowered op list into segments for the batched kernel (see Seg).  A run of RZ/CZ
-// becomes SEG_DIAG when it holds at least `min_diag_rz` RZ gates; a run of RY (or RX) gates on
-// distinct qubits becomes SEG_RLAYER when it holds at least `min_layer` gates (and at most
-// kMaxLayer); a run of two or more CNOT/X gates becomes SEG_PERM; everything else is
-// SEG_GATES.  Returns the number of checkpoints used.
+// becomes SEG_DIAG when it holds at least `min_diag_rz` RZ gates (and at most kMaxLayer RZ and
+// kMaxLayer CZ gates); a run of RY (or RX) gates on distinct qubits becomes SEG_RLAYER when it
+// holds at least `min_layer` gates (and at most kMaxLayer); a run of two to kMaxPerm CNOT/X
+// gates becomes SEG_PERM; a SEG_DIAG directly followed by a SEG_PERM becomes one
+// SEG_DIAGPERM; everything else is SEG_GATES.  Returns the number of checkpoints used.
 constexpr int kMaxLayer = 16;
 int segment_ops(const std::vector<DOp>& ops, int min_layer, int min_diag_rz,
                 std::vector<Seg>& segs);

@@ -39,8 +39,10 @@ struct TeamS {
   int rz_bit[kM];
   uint32_t cz_mask[kM];  // both-bits masks of the segment's CZ gates
   int n_cz;
-  uint32_t perm_lo[kMaxPerm];  // condition and flip masks of a permutation segment's gates
-  uint32_t perm_fl[kMaxPerm];
+  // A run of CNOT/X gates is an affine map of the index bits over GF(2), so its permutation
+  // is P(k) = pt_lo[k & 63] ^ pt_hi[k >> 6] (n <= 12), with pt_lo holding the constant part.
+  uint32_t pt_lo[64];
+  uint32_t pt_hi[64];
 };
 
 
@@ -57,13 +59,43 @@ struct Team {
   }
 };
 
-// Stage a permutation segment's (condition, flip) masks in shared memory.
-__device__ __forceinline__ void perm_setup(const Team& T, TeamS& S, const DOp* ops, const Seg& sg) {
-  if (T.rank < sg.count) {
-    S.perm_lo[T.rank] = (uint32_t)ops[sg.first + T.rank].lo_or;
-    S.perm_fl[T.rank] = (uint32_t)ops[sg.first + T.rank].flip;
+// The diagonal and permutation parts of a SEG_DIAGPERM segment.
+__device__ __forceinline__ Seg diag_part(const Seg& sg) {
+  Seg s = sg;
+  s.count = sg.split;
+  return s;
+}
+__device__ __forceinline__ Seg perm_part(const Seg& sg) {
+  Seg s = sg;
+  s.first = sg.first + sg.split;
+  s.count = sg.count - sg.split;
+  return s;
+}
+
+// Tabulate a permutation segment's map over the low and high six index bits: the gates'
+// conditional flips in order (inv = false: P) or in reverse order (inv = true: P^-1).
+__device__ __forceinline__ void perm_setup(const Team& T, TeamS& S, const DOp* ops, const Seg& sg,
+                                           bool inv) {
+  const DOp* g = ops + sg.first;
+  uint32_t c0 = 0;
+  for (int l = 0; l < sg.count; ++l) {
+    const DOp& o = g[inv ? sg.count - 1 - l : l];
+    if ((c0 & (uint32_t)o.lo_or) == (uint32_t)o.lo_or) c0 ^= (uint32_t)o.flip;
+  }
+  for (int j = T.rank; j < 128; j += T.size) {
+    uint32_t k = j < 64 ? (uint32_t)j : (uint32_t)(j - 64) << 6;
+    for (int l = 0; l < sg.count; ++l) {
+      const DOp& o = g[inv ? sg.count - 1 - l : l];
+      if ((k & (uint32_t)o.lo_or) == (uint32_t)o.lo_or) k ^= (uint32_t)o.flip;
+    }
+    if (j < 64) S.pt_lo[j] = k;
+    else S.pt_hi[j - 64] = k ^ c0;
   }
   T.sync();
+}
+
+__device__ __forceinline__ uint32_t perm_map(const TeamS& S, uint32_t k) {
+  return S.pt_lo[k & 63u] ^ S.pt_hi[k >> 6];
 }
 
 __device__ __forceinline__ uint32_t insert_zeros32(uint32_t p, const uint8_t* sb, int k) {
@@ -339,19 +371,33 @@ __device__ void run_instance(const BatchArgs& a, int idx, const Team& T, TeamS& 
     // ---------------------------------------------------------------- forward
     for (int s = 0; s < I.n_segs; ++s) {
       const Seg sg = segs[s];
-      if (sg.ckpt >= 0) {
+      if (sg.ckpt >= 0 && sg.kind != SEG_DIAGPERM) {
         team_copy(T, ck + (size_t)sg.ckpt * N, psi, N);
         T.sync();
       }
-      if (sg.kind == SEG_PERM) {
-        // psi'[j] = psi[P^-1 j] with P = C_last ... C_first (each CNOT/X is its own inverse)
-        perm_setup(T, S, ops, sg);
-        for (uint32_t j = tid; j < N; j += TS) {
-          uint32_t src = j;
-          for (int l = sg.count - 1; l >= 0; --l)
-            if ((src & S.perm_lo[l]) == S.perm_lo[l]) src ^= S.perm_fl[l];
-          lam[j] = psi[src];
+      if (sg.kind == SEG_DIAGPERM) {
+        // one pass: checkpoint psi[k], apply the phase, scatter to P k (the gates' conditional
+        // flips in order)
+        diag_setup(T, S, ops, diag_part(sg), theta, n);
+        perm_setup(T, S, ops, perm_part(sg), false);
+        const int ncz = S.n_cz;
+        double2* c = ck + (size_t)sg.ckpt * N;
+        for (uint32_t k = tid; k < N; k += TS) {
+          const double2 p0 = psi[k];
+          c[k] = p0;
+          const double2 ph = cmul(S.th[k >> hl], S.tl[k & lmask]);
+          double2 v = cmul(p0, ph);
+          if (ncz && cz_sign(S, ncz, k)) v = make_double2(dneg(v.x), dneg(v.y));
+          lam[perm_map(S, k)] = v;
         }
+        T.sync();
+        double2* t = psi;
+        psi = lam;
+        lam = t;
+      } else if (sg.kind == SEG_PERM) {
+        // psi'[j] = psi[P^-1 j] with P = C_last ... C_first (each CNOT/X is its own inverse)
+        perm_setup(T, S, ops, sg, true);
+        for (uint32_t j = tid; j < N; j += TS) lam[j] = psi[perm_map(S, j)];
         T.sync();
         double2* t = psi;
         psi = lam;
@@ -474,13 +520,8 @@ __device__ void run_instance(const BatchArgs& a, int idx, const Team& T, TeamS& 
       if (sg.kind == SEG_PERM) {
         // lambda_before[j] = lambda_after[P j], gathered into the psi buffer (psi is reloaded
         // from the checkpoint below), then the buffers swap roles
-        perm_setup(T, S, ops, sg);
-        for (uint32_t j = tid; j < N; j += TS) {
-          uint32_t dst = j;
-          for (int l = 0; l < sg.count; ++l)
-            if ((dst & S.perm_lo[l]) == S.perm_lo[l]) dst ^= S.perm_fl[l];
-          psi[j] = lam[dst];
-        }
+        perm_setup(T, S, ops, sg, false);
+        for (uint32_t j = tid; j < N; j += TS) psi[j] = lam[perm_map(S, j)];
         T.sync();
         double2* t = psi;
         psi = lam;
@@ -492,7 +533,56 @@ __device__ void run_instance(const BatchArgs& a, int idx, const Team& T, TeamS& 
       double v[kM];
 #pragma unroll
       for (int g = 0; g < kM; ++g) v[g] = 0.0;
-      if (sg.kind == SEG_RLAYER) {
+      if (sg.kind == SEG_DIAGPERM) {
+        // psi and lambda at the diagonal part's end are psi[P k] and lambda[P k]: gather both,
+        // take the signed bit sums of w_k = Im(conj(lambda) psi) as for SEG_DIAG, and keep the
+        // un-phased lambda in registers until every gather of the team is done (at most kHU
+        // amplitudes per thread in every team class)
+        const int m = diag_setup(T, S, ops, diag_part(sg), theta, n);
+        perm_setup(T, S, ops, perm_part(sg), false);
+        const int ncz = S.n_cz;
+        constexpr int kHB = 4;
+        constexpr int kHU = 16;
+        const int nhb = n - T.log_size;
+        double W = 0.0, hb[kHB] = {0.0, 0.0, 0.0, 0.0};
+        double2 lr[kHU];
+#pragma unroll
+        for (int u = 0; u < kHU; ++u) {
+          const uint32_t k = tid + u * TS;
+          if (k < N) {
+            const uint32_t src = perm_map(S, k);
+            const double2 pk = psi[src];
+            double2 lk = lam[src];
+            const double w = fma(lk.x, pk.y, dneg(lk.y) * pk.x);
+            W += w;
+#pragma unroll
+            for (int q = 0; q < kHB; ++q)
+              if (q < nhb) hb[q] += ((k >> (T.log_size + q)) & 1u) ? dneg(w) : w;
+            const double2 ph = cmul(S.th[k >> hl], S.tl[k & lmask]);
+            lk = cmul_conj(lk, ph);
+            if (ncz && cz_sign(S, ncz, k)) lk = make_double2(dneg(lk.x), dneg(lk.y));
+            lr[u] = lk;
+          }
+        }
+        T.sync();
+#pragma unroll
+        for (int u = 0; u < kHU; ++u) {
+          const uint32_t k = tid + u * TS;
+          if (k < N) lam[k] = lr[u];
+        }
+#pragma unroll
+        for (int g = 0; g < kM; ++g) {
+          if (g >= m) break;
+          const int b = S.rz_bit[g];
+          double val = (((uint32_t)tid >> (b < T.log_size ? b : 0)) & 1u) ? dneg(W) : W;
+#pragma unroll
+          for (int q = 0; q < kHB; ++q)
+            if (b == T.log_size + q) val = hb[q];
+          v[g] = val;
+        }
+        const double tot = team_sum16(T, S, v, m);
+        if (tid < m) contrib[S.rz_op[tid]] = tot;
+      } else if (sg.kind == SEG_RLAYER) {
         // gradients of every gate from (psi, lambda) at the layer's end, two gates per pass:
         // each thread reads a block of four amplitudes of psi and lambda and accumulates both
         // gates' pair terms from it

@@ -62,9 +62,16 @@ static_assert(sizeof(DGroup) == 32, "DGroup layout");
 //   SEG_PERM  : CNOT and X gates: their product is one permutation of basis indices, applied
 //               as a single gather into the other buffer (the psi and lambda buffers then swap
 //               roles); the sweep gathers lambda back and reloads psi from a checkpoint.
-enum { SEG_GATES = 0, SEG_RLAYER = 1, SEG_DIAG = 2, SEG_PERM = 3 };
+//   SEG_DIAGPERM: a SEG_DIAG run (its first `split` ops) directly followed by a SEG_PERM run
+//               (the pattern of every hardware-efficient layer), done in one pass each way: the
+//               forward pass writes the checkpoint, applies the phase and scatters to the
+//               permuted index; the sweep gathers lambda and psi through the permutation,
+//               takes the diagonal gradients, un-applies the phase to lambda and reloads psi
+//               from the one checkpoint.
+enum { SEG_GATES = 0, SEG_RLAYER = 1, SEG_DIAG = 2, SEG_PERM = 3, SEG_DIAGPERM = 4 };
 struct Seg {
-  int32_t kind;
+  int16_t kind;
+  int16_t split;  // SEG_DIAGPERM: ops of the diagonal part; else 0
   int32_t first;  // first op
   int32_t count;  // number of ops
   int32_t ckpt;   // checkpoint slot of psi before the segment, or -1
