@@ -39,6 +39,9 @@ struct TeamS {
   int rz_bit[kM];
   uint32_t cz_mask[kM];  // both-bits masks of the segment's CZ gates
   int n_cz;
+  int n_rz;
+  uint32_t pm_lo[kMaxPerm];  // condition and flip masks of a permutation segment's gates
+  uint32_t pm_fl[kMaxPerm];
   // A run of CNOT/X gates is an affine map of the index bits over GF(2), so its permutation
   // is P(k) = pt_lo[k & 63] ^ pt_hi[k >> 6] (n <= 12), with pt_lo holding the constant part.
   uint32_t pt_lo[64];
@@ -73,21 +76,24 @@ __device__ __forceinline__ Seg perm_part(const Seg& sg) {
 }
 
 // Tabulate a permutation segment's map over the low and high six index bits: the gates'
-// conditional flips in order (inv = false: P) or in reverse order (inv = true: P^-1).
+// conditional flips in order (inv = false: P) or in reverse order (inv = true: P^-1).  The
+// gates' masks are loaded in parallel (one lane per gate, at most kMaxPerm) and staged first.
 __device__ __forceinline__ void perm_setup(const Team& T, TeamS& S, const DOp* ops, const Seg& sg,
                                            bool inv) {
-  const DOp* g = ops + sg.first;
-  uint32_t c0 = 0;
-  for (int l = 0; l < sg.count; ++l) {
-    const DOp& o = g[inv ? sg.count - 1 - l : l];
-    if ((c0 & (uint32_t)o.lo_or) == (uint32_t)o.lo_or) c0 ^= (uint32_t)o.flip;
+  if (T.rank < sg.count) {
+    const DOp& o = ops[sg.first + T.rank];
+    const int l = inv ? sg.count - 1 - T.rank : T.rank;
+    S.pm_lo[l] = (uint32_t)o.lo_or;
+    S.pm_fl[l] = (uint32_t)o.flip;
   }
+  T.sync();
+  uint32_t c0 = 0;
+  for (int l = 0; l < sg.count; ++l)
+    if ((c0 & S.pm_lo[l]) == S.pm_lo[l]) c0 ^= S.pm_fl[l];
   for (int j = T.rank; j < 128; j += T.size) {
     uint32_t k = j < 64 ? (uint32_t)j : (uint32_t)(j - 64) << 6;
-    for (int l = 0; l < sg.count; ++l) {
-      const DOp& o = g[inv ? sg.count - 1 - l : l];
-      if ((k & (uint32_t)o.lo_or) == (uint32_t)o.lo_or) k ^= (uint32_t)o.flip;
-    }
+    for (int l = 0; l < sg.count; ++l)
+      if ((k & S.pm_lo[l]) == S.pm_lo[l]) k ^= S.pm_fl[l];
     if (j < 64) S.pt_lo[j] = k;
     else S.pt_hi[j - 64] = k ^ c0;
   }
@@ -287,32 +293,39 @@ __device__ __forceinline__ void op_pass2(const Team& T, double2* v, uint32_t N, 
 
 // Build the diagonal segment's half tables: th[hi] * tl[lo] = prod_RZ e^{-i phi s(k)}, and
 // the list of its CZ masks.
-__device__ __forceinline__ int diag_setup(const Team& T, TeamS& S, const DOp* ops,
+__device__ __noinline__ int diag_setup(const Team& T, TeamS& S, const DOp* ops,
                                           const Seg& sg, const double* theta, int n) {
-  int m = 0, ncz = 0;
-  for (int l = 0; l < sg.count; ++l) {
-    const int type = ops[sg.first + l].type;
+  // The segment's ops (at most kM RZ and kM CZ gates) are read in parallel by the lanes of the
+  // team's first warp; a ballot gives each RZ (CZ) gate its slot in gate order.
+  if (T.w == 0) {
+    const int lane = threadIdx.x & 31;
+    int type = -1;
+    DOp op;
+    if (lane < sg.count) {
+      op = ops[sg.first + lane];
+      type = op.type;
+    }
+    const unsigned brz = __ballot_sync(kFull, type == SV_GATE_RZ);
+    const unsigned bcz = __ballot_sync(kFull, type == SV_GATE_CZ);
+    const unsigned below = (1u << lane) - 1u;
     if (type == SV_GATE_RZ) {
-      if (T.rank == 0) {
-        S.rz_op[m] = sg.first + l;
-        S.rz_bit[m] = ops[sg.first + l].bit0;
-      }
-      ++m;
-    } else if (type == SV_GATE_CZ && ncz < kM) {
-      if (T.rank == 0) S.cz_mask[ncz] = (uint32_t)ops[sg.first + l].lo_or;
-      ++ncz;
+      const int i = __popc(brz & below);
+      S.rz_op[i] = sg.first + lane;
+      S.rz_bit[i] = op.bit0;
+      const double t = op.param >= 0 ? theta[op.param] : op.fixed;
+      double sn, cs;
+      sincos(0.5 * t, &sn, &cs);
+      S.cs[i] = make_double2(cs, sn);
+    } else if (type == SV_GATE_CZ) {
+      S.cz_mask[__popc(bcz & below)] = (uint32_t)op.lo_or;
+    }
+    if (lane == 0) {
+      S.n_rz = __popc(brz);
+      S.n_cz = __popc(bcz);
     }
   }
-  if (T.rank == 0) S.n_cz = ncz;
   T.sync();
-  if (T.rank < m) {
-    const DOp op = ops[S.rz_op[T.rank]];
-    const double t = op.param >= 0 ? theta[op.param] : op.fixed;
-    double sn, cs;
-    sincos(0.5 * t, &sn, &cs);
-    S.cs[T.rank] = make_double2(cs, sn);
-  }
-  T.sync();
+  const int m = S.n_rz;
   const int hl = n < 6 ? n : 6;
   const int nl = 1 << hl, nh = 1 << (n - hl);
   for (int j = T.rank; j < nl + nh; j += T.size) {
@@ -330,6 +343,21 @@ __device__ __forceinline__ int diag_setup(const Team& T, TeamS& S, const DOp* op
   }
   T.sync();
   return m;
+}
+
+// The fields of a group record that lambda = H psi uses (indices fit 32 bits: n <= 12).
+struct GRec {
+  uint32_t x, zu;
+  int cls;
+  int64_t toff;
+};
+__device__ __forceinline__ GRec grec(const DGroup& G) {
+  GRec r;
+  r.x = (uint32_t)G.x;
+  r.zu = (uint32_t)G.zu;
+  r.cls = G.cls;
+  r.toff = G.toff;
+  return r;
 }
 
 // Sign of the CZ gates of a diagonal segment at amplitude k (true = negative).
@@ -440,11 +468,24 @@ __device__ void run_instance(const BatchArgs& a, int idx, const Team& T, TeamS& 
       double2 acc[kHU];
 #pragma unroll
       for (int u = 0; u < kHU; ++u) acc[u] = make_double2(0.0, 0.0);
-      for (int g = 0; g < I.n_groups; ++g) {
-        const DGroup G = groups[g];
-        const uint32_t x = (uint32_t)G.x, zu = (uint32_t)G.zu;
+      // group records are loaded two groups ahead and the first table entry (a single-term
+      // group's coefficient) one group ahead, so neither load waits in the loop
+      const int ng = I.n_groups;
+      GRec Gn, Gnn;
+      double2 cn = make_double2(0.0, 0.0);
+      if (ng > 0) {
+        Gn = grec(groups[0]);
+        Gnn = grec(groups[ng > 1 ? 1 : 0]);
+        cn = a.tables[Gn.toff];
+      }
+      for (int g = 0; g < ng; ++g) {
+        const GRec G = Gn;
+        const double2 c = cn;
+        Gn = Gnn;
+        cn = a.tables[Gn.toff];
+        Gnn = grec(groups[g + 2 < ng ? g + 2 : ng - 1]);
+        const uint32_t x = G.x, zu = G.zu;
         if (G.cls >= 4) {
-          const double2 c = a.tables[G.toff];
           const int cls = G.cls - 4;
 #pragma unroll
           for (int u = 0; u < kHU; ++u) {
