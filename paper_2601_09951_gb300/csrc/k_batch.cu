@@ -28,6 +28,13 @@ constexpr unsigned kFull = 0xffffffffu;
 constexpr int kM = 16;  // values reduced at once (kMaxLayer)
 constexpr int kWarps = kBatchThreads / 32;
 
+// A single-qubit gate of a commuting layer: its coefficients, type and qubit bit.
+struct LOp {
+  Rot r;
+  int type;
+  int bit;
+};
+
 // Per-team scratch in static shared memory.
 struct TeamS {
   double red[kWarps];
@@ -42,6 +49,7 @@ struct TeamS {
   int n_rz;
   uint32_t pm_lo[kMaxPerm];  // condition and flip masks of a permutation segment's gates
   uint32_t pm_fl[kMaxPerm];
+  LOp lop[kM];               // the gates of a commuting layer, staged once per segment
   // A run of CNOT/X gates is an affine map of the index bits over GF(2), so its permutation
   // is P(k) = pt_lo[k & 63] ^ pt_hi[k >> 6] (n <= 12), with pt_lo holding the constant part.
   uint32_t pt_lo[64];
@@ -260,29 +268,74 @@ __device__ __forceinline__ void team_copy(const Team& T, double2* dst, const dou
   for (; k < N; k += s) dst[k] = src[k];
 }
 
-// Apply two single-qubit ops on distinct bits in one pass: each thread takes the four
-// amplitudes of a block (both bits 0, either, both 1), rotates them for the first op, then for
-// the second, in registers.  Half the barriers and shared-memory traffic of two op_pass calls.
-__device__ __forceinline__ void op_pass2(const Team& T, double2* v, uint32_t N, const DOp& o1,
-                                         const Rot& r1, const DOp& o2, const Rot& r2, bool inv) {
-  const uint32_t b1 = (uint32_t)o1.flip, b2 = (uint32_t)o2.flip;
+// Start an asynchronous copy of N amplitudes from global memory into the team's shared buffer
+// (16 B per cp.async, L2 only); async_wait() and a team barrier complete it.
+__device__ __forceinline__ void async_copy(const Team& T, double2* dst, const double2* src,
+                                           uint32_t N) {
+  for (uint32_t k = T.rank; k < N; k += T.size) {
+    const uint32_t d = (uint32_t)__cvta_generic_to_shared(dst + k);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d), "l"(src + k) : "memory");
+  }
+  asm volatile("cp.async.commit_group;" ::: "memory");
+}
+__device__ __forceinline__ void async_wait() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
+// Stage a commuting layer's gates (coefficients, type, bit) in shared memory: one parallel
+// load per gate instead of one dependent load per pass.
+__device__ __forceinline__ void layer_setup(const Team& T, TeamS& S, const DOp* ops,
+                                            const Rot* coef, const Seg& sg) {
+  if (T.rank < sg.count) {
+    LOp o;
+    o.r = coef[sg.first + T.rank];
+    o.type = ops[sg.first + T.rank].type;
+    o.bit = ops[sg.first + T.rank].bit0;
+    S.lop[T.rank] = o;
+  }
+  T.sync();
+}
+
+// One staged layer gate on v (inv: its inverse).
+__device__ __forceinline__ void lop_pass(const Team& T, double2* v, uint32_t N, const LOp& o,
+                                         bool inv) {
+  const uint32_t fl = 1u << o.bit, low = fl - 1u;
+  for (uint32_t p = T.rank; p < (N >> 1); p += T.size) {
+    const uint32_t i = ((p & ~low) << 1) | (p & low);
+    double2 x = v[i], y = v[i | fl];
+    pair_apply(o.type, o.r, inv, x, y);
+    v[i] = x;
+    v[i | fl] = y;
+  }
+}
+
+// Two staged layer gates on distinct bits in one pass (as op_pass2).  If ckout is set, the
+// amplitudes are also stored there unchanged first: the pass doubles as the checkpoint copy.
+__device__ __forceinline__ void lop_pass2(const Team& T, double2* v, uint32_t N, const LOp& o1,
+                                          const LOp& o2, bool inv, double2* ckout) {
+  const uint32_t b1 = 1u << o1.bit, b2 = 1u << o2.bit;
   uint8_t sb[2];
-  sb[0] = (uint8_t)min(o1.bit0, o2.bit0);
-  sb[1] = (uint8_t)max(o1.bit0, o2.bit0);
-  const uint32_t nb = N >> 2;
-  for (uint32_t p = T.rank; p < nb; p += T.size) {
+  sb[0] = (uint8_t)min(o1.bit, o2.bit);
+  sb[1] = (uint8_t)max(o1.bit, o2.bit);
+  const Rot r1 = o1.r, r2 = o2.r;
+  const int t1 = o1.type, t2 = o2.type;
+  for (uint32_t p = T.rank; p < (N >> 2); p += T.size) {
     const uint32_t i = insert_zeros32(p, sb, 2);
     double2 a = v[i], b = v[i | b1], c = v[i | b2], d = v[i | b1 | b2];
+    if (ckout) {
+      ckout[i] = a;
+      ckout[i | b1] = b;
+      ckout[i | b2] = c;
+      ckout[i | b1 | b2] = d;
+    }
     if (!inv) {
-      pair_apply(o1.type, r1, false, a, b);
-      pair_apply(o1.type, r1, false, c, d);
-      pair_apply(o2.type, r2, false, a, c);
-      pair_apply(o2.type, r2, false, b, d);
+      pair_apply(t1, r1, false, a, b);
+      pair_apply(t1, r1, false, c, d);
+      pair_apply(t2, r2, false, a, c);
+      pair_apply(t2, r2, false, b, d);
     } else {
-      pair_apply(o2.type, r2, true, a, c);
-      pair_apply(o2.type, r2, true, b, d);
-      pair_apply(o1.type, r1, true, a, b);
-      pair_apply(o1.type, r1, true, c, d);
+      pair_apply(t2, r2, true, a, c);
+      pair_apply(t2, r2, true, b, d);
+      pair_apply(t1, r1, true, a, b);
+      pair_apply(t1, r1, true, c, d);
     }
     v[i] = a;
     v[i | b1] = b;
@@ -399,7 +452,7 @@ __device__ void run_instance(const BatchArgs& a, int idx, const Team& T, TeamS& 
     // ---------------------------------------------------------------- forward
     for (int s = 0; s < I.n_segs; ++s) {
       const Seg sg = segs[s];
-      if (sg.ckpt >= 0 && sg.kind != SEG_DIAGPERM) {
+      if (sg.ckpt >= 0 && sg.kind != SEG_DIAGPERM && sg.kind != SEG_RLAYER) {
         team_copy(T, ck + (size_t)sg.ckpt * N, psi, N);
         T.sync();
       }
@@ -441,13 +494,16 @@ __device__ void run_instance(const BatchArgs& a, int idx, const Team& T, TeamS& 
         }
         T.sync();
       } else if (sg.kind == SEG_RLAYER) {
-        int l = sg.first;
-        for (; l + 1 < sg.first + sg.count; l += 2) {
-          op_pass2(T, psi, N, ops[l], coef[l], ops[l + 1], coef[l + 1], false);
+        // the layer's first pass also writes the checkpoint (a layer has at least two gates)
+        layer_setup(T, S, ops, coef, sg);
+        int g = 0;
+        for (; g + 1 < sg.count; g += 2) {
+          lop_pass2(T, psi, N, S.lop[g], S.lop[g + 1], false,
+                    g == 0 ? ck + (size_t)sg.ckpt * N : nullptr);
           T.sync();
         }
-        if (l < sg.first + sg.count) {
-          op_pass(T, psi, N, ops[l], coef[l], false);
+        if (g < sg.count) {
+          lop_pass(T, psi, N, S.lop[g], false);
           T.sync();
         }
       } else {
@@ -606,6 +662,8 @@ __device__ void run_instance(const BatchArgs& a, int idx, const Team& T, TeamS& 
           }
         }
         T.sync();
+        // psi before the segment: the checkpoint copy overlaps the stores and the reduction
+        async_copy(T, psi, ck + (size_t)sg.ckpt * N, N);
 #pragma unroll
         for (int u = 0; u < kHU; ++u) {
           const uint32_t k = tid + u * TS;
@@ -623,17 +681,22 @@ __device__ void run_instance(const BatchArgs& a, int idx, const Team& T, TeamS& 
         }
         const double tot = team_sum16(T, S, v, m);
         if (tid < m) contrib[S.rz_op[tid]] = tot;
+        async_wait();
+        T.sync();
+        continue;
       } else if (sg.kind == SEG_RLAYER) {
         // gradients of every gate from (psi, lambda) at the layer's end, two gates per pass:
         // each thread reads a block of four amplitudes of psi and lambda and accumulates both
         // gates' pair terms from it
+        layer_setup(T, S, ops, coef, sg);
         int g = 0;
         for (; g + 1 < sg.count; g += 2) {
-          const DOp o1 = ops[sg.first + g], o2 = ops[sg.first + g + 1];
-          const uint32_t b1 = (uint32_t)o1.flip, b2 = (uint32_t)o2.flip;
+          const LOp& o1 = S.lop[g];
+          const LOp& o2 = S.lop[g + 1];
+          const uint32_t b1 = 1u << o1.bit, b2 = 1u << o2.bit;
           uint8_t sb[2];
-          sb[0] = (uint8_t)min(o1.bit0, o2.bit0);
-          sb[1] = (uint8_t)max(o1.bit0, o2.bit0);
+          sb[0] = (uint8_t)min(o1.bit, o2.bit);
+          sb[1] = (uint8_t)max(o1.bit, o2.bit);
           double a1 = 0.0, a2 = 0.0;
           for (uint32_t p = tid; p < (N >> 2); p += TS) {
             const uint32_t i = insert_zeros32(p, sb, 2);
@@ -651,12 +714,12 @@ __device__ void run_instance(const BatchArgs& a, int idx, const Team& T, TeamS& 
           }
         }
         if (g < sg.count) {
-          const DOp op = ops[sg.first + g];
-          const uint32_t fl = (uint32_t)op.flip;
+          const LOp& o = S.lop[g];
+          const uint32_t fl = 1u << o.bit, low = fl - 1u;
           double acc = 0.0;
           for (uint32_t p = tid; p < (N >> 1); p += TS) {
-            const uint32_t i = insert_zeros32(p, op.sb, 1);
-            pair_grad_acc(op.type, lam[i], lam[i ^ fl], psi[i], psi[i ^ fl], acc);
+            const uint32_t i = ((p & ~low) << 1) | (p & low);
+            pair_grad_acc(o.type, lam[i], lam[i | fl], psi[i], psi[i | fl], acc);
           }
 #pragma unroll
           for (int q = 0; q < kM; ++q)
@@ -664,16 +727,21 @@ __device__ void run_instance(const BatchArgs& a, int idx, const Team& T, TeamS& 
         }
         const double tot = team_sum16(T, S, v, sg.count);
         if (tid < sg.count) contrib[sg.first + tid] = tot;
-        // un-apply the layer to lambda (its gates commute: pairs in forward order, inverted)
-        int l = sg.first;
-        for (; l + 1 < sg.first + sg.count; l += 2) {
-          op_pass2(T, lam, N, ops[l], coef[l], ops[l + 1], coef[l + 1], true);
+        // psi before the layer: the checkpoint copy runs while the layer is un-applied to
+        // lambda (its gates commute: pairs in forward order, inverted), which leaves psi alone
+        async_copy(T, psi, ck + (size_t)sg.ckpt * N, N);
+        g = 0;
+        for (; g + 1 < sg.count; g += 2) {
+          lop_pass2(T, lam, N, S.lop[g], S.lop[g + 1], true, nullptr);
           T.sync();
         }
-        if (l < sg.first + sg.count) {
-          op_pass(T, lam, N, ops[l], coef[l], true);
+        if (g < sg.count) {
+          lop_pass(T, lam, N, S.lop[g], true);
           T.sync();
         }
+        async_wait();
+        T.sync();
+        continue;
       } else {  // SEG_DIAG
         const int m = diag_setup(T, S, ops, sg, theta, n);
         const int ncz = S.n_cz;
