@@ -124,7 +124,7 @@ sv_status lower_circuit(const sv_circuit* c, int expect_n, HostCircuit& out) {
   return SV_OK;
 }
 
-int segment_ops(const std::vector<DOp>& ops, int min_layer, int min_diag_rz,
+int segment_ops(std::vector<DOp>& ops, int min_layer, int min_diag_rz,
                 std::vector<Seg>& segs) {
   segs.clear();
   int ckpt = 0;
@@ -198,6 +198,13 @@ int segment_ops(const std::vector<DOp>& ops, int min_layer, int min_diag_rz,
   ckpt = 0;
   for (Seg& s : merged) s.ckpt = s.kind == SEG_GATES ? -1 : ckpt++;
   segs.swap(merged);
+  for (DOp& op : ops) op.flags &= ~kOpDiagCS;
+  for (const Seg& s : segs) {
+    if (s.kind != SEG_DIAG && s.kind != SEG_DIAGPERM) continue;
+    const int nd = s.kind == SEG_DIAG ? s.count : s.split;
+    for (int l = s.first; l < s.first + nd; ++l)
+      if (ops[l].type == SV_GATE_RZ) ops[l].flags |= kOpDiagCS;
+  }
   return ckpt;
 }
 

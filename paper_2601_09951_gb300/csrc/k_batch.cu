@@ -347,7 +347,7 @@ __device__ __forceinline__ void lop_pass2(const Team& T, double2* v, uint32_t N,
 // Build the diagonal segment's half tables: th[hi] * tl[lo] = prod_RZ e^{-i phi s(k)}, and
 // the list of its CZ masks.
 __device__ __noinline__ int diag_setup(const Team& T, TeamS& S, const DOp* ops,
-                                          const Seg& sg, const double* theta, int n) {
+                                          const Rot* coef, const Seg& sg, int n) {
   // The segment's ops (at most kM RZ and kM CZ gates) are read in parallel by the lanes of the
   // team's first warp; a ballot gives each RZ (CZ) gate its slot in gate order.
   if (T.w == 0) {
@@ -365,10 +365,8 @@ __device__ __noinline__ int diag_setup(const Team& T, TeamS& S, const DOp* ops,
       const int i = __popc(brz & below);
       S.rz_op[i] = sg.first + lane;
       S.rz_bit[i] = op.bit0;
-      const double t = op.param >= 0 ? theta[op.param] : op.fixed;
-      double sn, cs;
-      sincos(0.5 * t, &sn, &cs);
-      S.cs[i] = make_double2(cs, sn);
+      const Rot r = coef[sg.first + lane];  // (cos phi, sin phi), set up with the step's coefficients
+      S.cs[i] = make_double2(r.a, r.b);
     } else if (type == SV_GATE_CZ) {
       S.cz_mask[__popc(bcz & below)] = (uint32_t)op.lo_or;
     }
@@ -444,7 +442,19 @@ __device__ void run_instance(const BatchArgs& a, int idx, const Team& T, TeamS& 
   const double lr = per_inst ? I.lr : (a.lr_inst ? a.lr_inst[idx] : a.lr);
 
   for (int step = 0; step < steps; ++step) {
-    for (int g = tid; g < I.n_ops; g += TS) coef[g] = make_coef(ops[g], theta).r;
+    for (int g = tid; g < I.n_ops; g += TS) {
+      const DOp op = ops[g];
+      if (op.flags & kOpDiagCS) {
+        const double t = op.param >= 0 ? theta[op.param] : op.fixed;
+        Rot r;
+        sincos(0.5 * t, &r.b, &r.a);
+        r.k = 0;
+        r.pad = 0;
+        coef[g] = r;
+      } else {
+        coef[g] = make_coef(op, theta).r;
+      }
+    }
     for (uint32_t k = tid; k < N; k += TS)
       psi[k] = make_double2(k == (uint32_t)I.ref ? 1.0 : 0.0, 0.0);
     T.sync();
@@ -459,7 +469,7 @@ __device__ void run_instance(const BatchArgs& a, int idx, const Team& T, TeamS& 
       if (sg.kind == SEG_DIAGPERM) {
         // one pass: checkpoint psi[k], apply the phase, scatter to P k (the gates' conditional
         // flips in order)
-        diag_setup(T, S, ops, diag_part(sg), theta, n);
+        diag_setup(T, S, ops, coef, diag_part(sg), n);
         perm_setup(T, S, ops, perm_part(sg), false);
         const int ncz = S.n_cz;
         double2* c = ck + (size_t)sg.ckpt * N;
@@ -484,7 +494,7 @@ __device__ void run_instance(const BatchArgs& a, int idx, const Team& T, TeamS& 
         psi = lam;
         lam = t;
       } else if (sg.kind == SEG_DIAG) {
-        diag_setup(T, S, ops, sg, theta, n);
+        diag_setup(T, S, ops, coef, sg, n);
         const int ncz = S.n_cz;
         for (uint32_t k = tid; k < N; k += TS) {
           const double2 ph = cmul(S.th[k >> hl], S.tl[k & lmask]);
@@ -635,7 +645,7 @@ __device__ void run_instance(const BatchArgs& a, int idx, const Team& T, TeamS& 
         // take the signed bit sums of w_k = Im(conj(lambda) psi) as for SEG_DIAG, and keep the
         // un-phased lambda in registers until every gather of the team is done (at most kHU
         // amplitudes per thread in every team class)
-        const int m = diag_setup(T, S, ops, diag_part(sg), theta, n);
+        const int m = diag_setup(T, S, ops, coef, diag_part(sg), n);
         perm_setup(T, S, ops, perm_part(sg), false);
         const int ncz = S.n_cz;
         constexpr int kHB = 4;
@@ -743,7 +753,7 @@ __device__ void run_instance(const BatchArgs& a, int idx, const Team& T, TeamS& 
         T.sync();
         continue;
       } else {  // SEG_DIAG
-        const int m = diag_setup(T, S, ops, sg, theta, n);
+        const int m = diag_setup(T, S, ops, coef, sg, n);
         const int ncz = S.n_cz;
         // Signed sums per bit: the bits below log_size are fixed within a thread (one running
         // sum W suffices); at most kHB higher bits vary across the thread's amplitudes.

@@ -18,12 +18,16 @@ struct DOp {
   int32_t k;       // number of inserted zero bits
   int32_t bit0;    // basis-index bit of the first wire (1-qubit gates)
   uint8_t sb[4];   // sorted bit positions of the wires
-  int32_t pad;
+  int32_t flags;   // kOpDiagCS: an RZ gate of a batched diagonal segment (see below)
   uint64_t lo_or;  // bits set in the first amplitude of each pair
   uint64_t flip;   // XOR mask from the first to the second amplitude
   double fixed;    // angle when param < 0
 };
 static_assert(sizeof(DOp) == 48, "DOp layout");
+// The batched kernel applies the RZ gates of a diagonal segment as one phase and needs their
+// (cos phi, sin phi), phi = theta/2, rather than the lifting form: for an op with this flag its
+// coefficient slot holds Rot{a = cos phi, b = sin phi, k = 0}.
+constexpr int32_t kOpDiagCS = 1;
 
 // Lifting form of the rotation R(phi) = [[c, -s], [s, c]] (phi = theta/2):
 // R(phi) = L(a) S(b) L(a) R(k pi/2), a = -tan(r/2), b = sin(r), r = phi - k pi/2 in
