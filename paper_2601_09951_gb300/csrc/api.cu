@@ -731,6 +731,8 @@ sv_status sv_batch_create(const sv_instance* inst, int32_t n, void* stream, sv_b
     }
     pptr.push_back((int32_t)pops.size());
     const int64_t toff0 = (int64_t)tables.size();
+    B.tab_off = toff0;
+    B.tab_n = (int32_t)hh.tables.size();
     for (DGroup g : hh.groups) {
       g.toff += toff0;
       groups.push_back(g);

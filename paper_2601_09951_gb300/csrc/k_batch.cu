@@ -268,6 +268,13 @@ __device__ __forceinline__ void team_copy(const Team& T, double2* dst, const dou
   for (; k < N; k += s) dst[k] = src[k];
 }
 
+// Bring [p, p + bytes) into L2 ahead of use, one 128-byte line per prefetch across the team.
+__device__ __forceinline__ void team_prefetch_l2(const Team& T, const void* p, int64_t bytes) {
+  const char* b = (const char*)p;
+  for (int64_t o = (int64_t)T.rank * 128; o < bytes; o += (int64_t)T.size * 128)
+    asm volatile("prefetch.global.L2 [%0];" ::"l"(b + o));
+}
+
 // Start an asynchronous copy of N amplitudes from global memory into the team's shared buffer
 // (16 B per cp.async, L2 only); async_wait() and a team barrier complete it.
 __device__ __forceinline__ void async_copy(const Team& T, double2* dst, const double2* src,
@@ -457,6 +464,9 @@ __device__ void run_instance(const BatchArgs& a, int idx, const Team& T, TeamS& 
     }
     for (uint32_t k = tid; k < N; k += TS)
       psi[k] = make_double2(k == (uint32_t)I.ref ? 1.0 : 0.0, 0.0);
+    // the group records and tables are first read by lambda = H psi, after the forward pass
+    team_prefetch_l2(T, groups, (int64_t)I.n_groups * (int64_t)sizeof(DGroup));
+    team_prefetch_l2(T, a.tables + I.tab_off, (int64_t)I.tab_n * (int64_t)sizeof(double2));
     T.sync();
 
     // ---------------------------------------------------------------- forward

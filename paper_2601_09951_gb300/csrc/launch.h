@@ -55,14 +55,16 @@ cudaError_t launch_bpass(double2* psi, double2* lam, const FPass& P, const FItem
 // BatchArgs::n_steps < 0 (per-instance step counts, as the serving loop runs them).
 struct BInst {
   int32_t n, n_ops, n_groups, n_params, n_segs, n_ckpt;
-  int32_t steps, pad;
+  int32_t steps;
+  int32_t tab_n;  // the instance's group tables: tab_n double2 entries from tab_off
   uint64_t ref;
   int64_t op_off, grp_off, theta_off, seg_off, pp_off, etraj_off;
   int64_t coef_off, contrib_off;  // scratch offsets (Rot / double units)
   int64_t grad_off;               // gradient offset (double units)
   double lr;
+  int64_t tab_off;
 };
-static_assert(sizeof(BInst) == 120, "BInst layout");
+static_assert(sizeof(BInst) == 128, "BInst layout");
 
 // A work item of the batched kernel: one instance on the CTA's 8 warps (cls 0, n <= 12), two
 // instances on 4 warps each (cls 1, n <= 11) or eight on one warp each (cls 2, n <= 9); unused

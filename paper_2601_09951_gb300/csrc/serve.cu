@@ -249,6 +249,8 @@ sv_status place_small(sv_server* s, Req& r) {
   B.pp_off = (base + L.pptr) / 4;
   B.theta_off = (base + L.theta) / 8;
   B.grad_off = (base + L.grad) / 8;
+  B.tab_off = tables_elem;
+  B.tab_n = (int32_t)r.hh.tables.size();
   B.lr = r.lr;
   r.theta_elem = B.theta_off;
   r.etraj_elem = (base + L.etraj) / 8;
