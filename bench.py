@@ -40,7 +40,7 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", default="batch",
-                    choices=["batch", "serve", "kernels", "single", "h2"],
+                    choices=["batch", "serve", "kernels", "single", "h2", "classes"],
                     help="batch: the batched evaluation step (default); serve: the request "
                          "loop (latency percentiles), printed as its own JSON line")
     ap.add_argument("--requests", type=int, default=300)
@@ -234,7 +234,7 @@ HBM_PEAK_GBS = 6678.2  # measured copy bandwidth (read + write) on this machine's G
 # dram__bytes_read.sum + dram__bytes_write.sum of one k_batch launch of the default workload,
 # from the ncu capture recorded in profiles/k_batch_hea_batch.md, keyed by a hash of the
 # kernel's sources: once the kernel changes the key no longer matches and traffic is null.
-KBATCH_TRAFFIC = {"8f9067c8779f3d1a": 640.63e6 + 850.12e6}
+KBATCH_TRAFFIC = {"0816ef3ca60b3344": 402.80e6 + 524.97e6}
 KBATCH_SOURCES = ("k_batch.cu", "svqe_internal.cuh", "svqe_types.h", "launch.h")
 
 
@@ -374,6 +374,47 @@ def run_single(args):
                       "dtype": "f64"}), flush=True)
 
 
+def run_classes(args):
+    """Batched-kernel throughput by register size: for each n, a batch of instances of that n
+    alone (hardware-efficient ansatz, 5 layers, 275 terms), enough to give every CTA several
+    items of the n's team class.  One JSON line per n with its share of the FP64 peak."""
+    import torch
+    torch.cuda.set_device(0)
+    from paper_2601_09951_gb300 import build as libbuild
+    libbuild.build()
+    from paper_2601_09951_gb300 import svqe
+    from paper_2601_09951_gb300 import workloads as W
+    per_item = {12: 1, 11: 2, 10: 4}
+    for n in range(4, 13):
+        ninst = 152 * 4 * per_item.get(n, 8)
+        insts = [W.hea_instance(n, 5, 275, 77, stream=i + 1) for i in range(ninst)]
+        stream = torch.cuda.Stream()
+        b = svqe.Batch(insts, stream=stream.cuda_stream)
+        th = torch.tensor(b.theta_of(insts), dtype=torch.float64, device="cuda")
+        e = torch.empty(ninst, dtype=torch.float64, device="cuda")
+        g = torch.empty(b.n_params, dtype=torch.float64, device="cuda")
+        flops, _ = b.cost()
+        with torch.cuda.stream(stream):
+            for _ in range(max(3, args.warmup)):
+                b.run_dev(th.data_ptr(), e.data_ptr(), g.data_ptr())
+            torch.cuda.synchronize()
+            t0 = torch.cuda.Event(enable_timing=True)
+            t1 = torch.cuda.Event(enable_timing=True)
+            reps = max(1, min(args.steps, 20))
+            t0.record(stream)
+            for _ in range(reps):
+                b.run_dev(th.data_ptr(), e.data_ptr(), g.data_ptr())
+            t1.record(stream)
+            torch.cuda.synchronize()
+        ms = t0.elapsed_time(t1) / reps
+        tf = flops / (ms * 1e-3) / 1e12
+        print(json.dumps({"workload": f"hea_n{n}_L5_T275 x {ninst}", "n_qubits": n,
+                          "ms_per_step": ms, "evals_per_s": ninst / ms * 1e3,
+                          "fp64_tflops": tf, "frac_of_fp64_peak": tf / FP64_PEAK_TFLOPS}),
+              flush=True)
+        del b
+
+
 def run_h2(args):
     """The paper's H2 potential-energy-surface procedure (Sec. 2.2, 3.4; Algorithm 1): 100 bond
     lengths, Adam with alpha = 0.01 from theta = 0, 300 iterations (the HPC runs of Sec. 5.2),
@@ -434,7 +475,7 @@ def main():
     if args.workload != "batch":
         if rank == 0:
             {"serve": run_serve, "kernels": run_kernels, "single": run_single,
-             "h2": run_h2}[args.workload](args)
+             "h2": run_h2, "classes": run_classes}[args.workload](args)
         return
     import torch
     torch.cuda.set_device(local)

@@ -543,21 +543,19 @@ sv_status sv_state_device_ptr(sv_ctx* c, void** psi_dev) {
 // ------------------------------------------------------------------------------ batches
 static constexpr int kTableBitsBatch = SV_BATCH_MAX_QUBITS;  // full diagonal tables allowed
 
-// Team class of an instance: 0 (8 warps, n <= 12), 1 (4 warps, n <= 11), 2 (1 warp, n <= 9).
-int svqe::batch_class(int n) { return n <= kClassQubits[2] ? 2 : n <= kClassQubits[1] ? 1 : 0; }
-int svqe::class_teams(int n) {
-  const int c = batch_class(n);
-  return c == 0 ? 1 : c == 1 ? 2 : 8;
+// Team class of an instance (see kClassWarps).
+int svqe::batch_class(int n) {
+  return n <= kClassQubits[2] ? 2 : n <= kClassQubits[3] ? 3 : n <= kClassQubits[1] ? 1 : 0;
 }
+int svqe::class_teams(int n) { return 8 / kClassWarps[batch_class(n)]; }
 
-// Work items: class-0 instances alone, class-1 instances in pairs and class-2 instances in
-// groups of eight.  What sets an item's duration is the work of one thread of its slowest team,
+// Work items: one instance per team of its class (one, two, eight or four per item).  What sets an item's duration is the work of one thread of its slowest team,
 // not the item's flops (eight 9-qubit instances on one warp each take about as long as one
 // 12-qubit instance on eight warps), so instances are ordered by that estimate -- amplitudes per
 // thread times the per-amplitude work of the ops and groups, plus a per-op latency term -- and
 // items by the estimate of their first (slowest) instance, slowest first.
 static double thread_time(const BInst& B, double cost) {
-  const int team = 32 * (batch_class(B.n) == 0 ? 8 : batch_class(B.n) == 1 ? 4 : 1);
+  const int team = 32 * kClassWarps[batch_class(B.n)];
   const double per_thread = std::max(1.0, (double)(1u << B.n) / team);
   (void)cost;
   return per_thread * (6.0 * B.n_ops + 2.0 * B.n_groups + 8.0) + 150.0 * B.n_ops;
@@ -572,14 +570,15 @@ std::vector<BItem> svqe::batch_items(const std::vector<BInst>& bi, const std::ve
   std::stable_sort(order.begin(), order.end(), [&](int a, int c) { return cost[a] > cost[c]; });
   std::vector<BItem> items;
   std::vector<double> icost;
-  BItem open[3];
-  int fill[3] = {0, 0, 0};
-  const int cap[3] = {1, 2, 8};
-  for (int c = 0; c < 3; ++c) {
+  BItem open[kNumClasses];
+  int fill[kNumClasses], cap[kNumClasses];
+  for (int c = 0; c < kNumClasses; ++c) {
     open[c].cls = c;
     for (int t = 0; t < 8; ++t) open[c].inst[t] = -1;
+    fill[c] = 0;
+    cap[c] = 8 / kClassWarps[c];
   }
-  std::vector<double> first_cost(3, 0.0);
+  std::vector<double> first_cost(kNumClasses, 0.0);
   for (int i : order) {
     const int c = batch_class(bi[i].n);
     if (fill[c] == 0) first_cost[c] = cost[i];
@@ -591,7 +590,7 @@ std::vector<BItem> svqe::batch_items(const std::vector<BInst>& bi, const std::ve
       for (int t = 0; t < 8; ++t) open[c].inst[t] = -1;
     }
   }
-  for (int c = 0; c < 3; ++c)
+  for (int c = 0; c < kNumClasses; ++c)
     if (fill[c] > 0) {
       items.push_back(open[c]);
       icost.push_back(first_cost[c]);

@@ -3,9 +3,10 @@
 //
 // A CTA (8 warps) takes work items from a cost-sorted queue with an atomic counter (largest
 // first, so the tail is made of cheap items).  An item is one 12-qubit instance run by all 8
-// warps, two instances of 10-11 qubits run by 4 warps each, or eight instances of at most 9
-// qubits run by one warp each: every instance gets at most 16 amplitudes per thread, and small
-// instances synchronise with __syncwarp or a named barrier instead of the whole CTA.  An
+// warps, two 11-qubit instances on 4 warps each, four 10-qubit instances on 2 warps each, or
+// eight instances of at most 9 qubits on one warp each: every instance gets at most 16
+// amplitudes per thread, and small instances synchronise with __syncwarp or a named barrier
+// instead of the whole CTA.  An
 // instance's psi and lambda (2 x 2^n x 16 bytes) live in its team's share of shared memory for
 // the forward pass, lambda = H psi and the adjoint sweep.  GB300's FP64 pipe (2 DFMA/clk/SM) is the binding resource, so the
 // op list is executed in segments (see Seg) that cut FP64 work:
@@ -847,13 +848,13 @@ __global__ void __launch_bounds__(kBatchThreads, 1) k_batch(BatchArgs a) {
     __syncthreads();
     if (item >= a.n_items) break;
     const int cls = a.items[item].cls;
-    // team layout of the item's class: 1 x 8 warps, 2 x 4 warps or 8 x 1 warp
-    const int nw = cls == 0 ? kWarps : cls == 1 ? kWarps / 2 : 1;
+    // team layout of the item's class (kClassWarps): 1 x 8, 2 x 4, 8 x 1 or 4 x 2 warps
+    const int nw = cls == 0 ? 8 : cls == 1 ? 4 : cls == 3 ? 2 : 1;
     const int team = wi / nw;
     Team T;
     T.nw = nw;
     T.size = nw * 32;
-    T.log_size = nw == 8 ? 8 : nw == 4 ? 7 : 5;
+    T.log_size = nw == 8 ? 8 : nw == 4 ? 7 : nw == 2 ? 6 : 5;
     T.rank = threadIdx.x - team * T.size;
     T.w = wi - team * nw;
     T.bar = 1 + team;

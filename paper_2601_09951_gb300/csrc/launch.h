@@ -66,15 +66,20 @@ struct BInst {
 };
 static_assert(sizeof(BInst) == 128, "BInst layout");
 
-// A work item of the batched kernel: one instance on the CTA's 8 warps (cls 0, n <= 12), two
-// instances on 4 warps each (cls 1, n <= 11) or eight on one warp each (cls 2, n <= 9); unused
-// entries of inst are -1.
+// A work item of the batched kernel: the instances of one team class (see kClassWarps), one
+// per team; unused entries of inst are -1.
 struct BItem {
   int32_t cls;
   int32_t inst[8];
 };
 static_assert(sizeof(BItem) == 36, "BItem layout");
-constexpr int kClassQubits[3] = {12, 11, 9};
+// Team classes of the batched kernel (8 warps per CTA): warps per team and the largest
+// instance each class runs, so that every thread holds at most 16 of the 2^n amplitudes.
+//   class 0: one team of 8 warps, n = 12;   class 1: two teams of 4 warps, n = 11;
+//   class 2: eight teams of 1 warp, n <= 9; class 3: four teams of 2 warps, n = 10.
+constexpr int kNumClasses = 4;
+constexpr int kClassWarps[kNumClasses] = {8, 4, 1, 2};
+constexpr int kClassQubits[kNumClasses] = {12, 11, 9, 10};
 
 struct BatchArgs {
   const BInst* inst;
