@@ -606,7 +606,8 @@ std::vector<BItem> svqe::batch_items(const std::vector<BInst>& bi, const std::ve
 // FP64 flops (FMA = 2) of one instance's forward pass, lambda = H psi and adjoint sweep, as
 // k_batch executes its segments: lifting rotation 12 per pair, gradient 8 per pair, H gate 8
 // per pair; a diagonal segment (alone or fused with the permutation after it) 12 per
-// amplitude forward and 16 + (RZ gates on bits >= 8) backward; a commuting layer un-applies lambda only; groups 4 (real or imaginary table) or 8
+// amplitude forward and 16 + (RZ gates on bits >= 8) backward; a product layer 1 per amplitude
+// forward and its gradients (8 per pair) backward; a commuting layer un-applies lambda only; groups 4 (real or imaginary table) or 8
 // (complex) per amplitude plus 4 for the energy.
 double svqe::batch_instance_flops(const HostCircuit& hc, const HostHam& hh,
                             const std::vector<Seg>& segs) {
@@ -621,9 +622,10 @@ double svqe::batch_instance_flops(const HostCircuit& hc, const HostHam& hh,
         if (rot) f += pairs * (12 + 24 + (op.param >= 0 ? 8 : 0));
         else if (op.type == SV_GATE_H) f += pairs * (8 + 16);
       } else if (s.kind == SEG_RLAYER) {
-        f += pairs * (12 + 8 + 12);
+        f += pairs * (s.split == 1 ? 8 : 12 + 8 + 12);
       }
     }
+    if (s.kind == SEG_RLAYER && s.split == 1) f += N;  // the product state, one DMUL/amp
     if (s.kind == SEG_DIAG || s.kind == SEG_DIAGPERM) {
       int hi = 0;
       for (int l = s.first; l < s.first + s.count; ++l)

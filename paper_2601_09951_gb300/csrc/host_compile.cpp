@@ -195,15 +195,26 @@ int segment_ops(std::vector<DOp>& ops, int min_layer, int min_diag_rz,
       merged.push_back(segs[s]);
     }
   }
+  // A first segment made of RY gates acts on the reference basis state: a product layer.
+  if (!merged.empty() && merged[0].kind == SEG_RLAYER && merged[0].first == 0) {
+    bool ry = true;
+    for (int l = 0; l < merged[0].count; ++l) ry = ry && ops[l].type == SV_GATE_RY;
+    if (ry) merged[0].split = 1;
+  }
   ckpt = 0;
-  for (Seg& s : merged) s.ckpt = s.kind == SEG_GATES ? -1 : ckpt++;
+  for (Seg& s : merged)
+    s.ckpt = (s.kind == SEG_GATES || (s.kind == SEG_RLAYER && s.split == 1)) ? -1 : ckpt++;
   segs.swap(merged);
-  for (DOp& op : ops) op.flags &= ~kOpDiagCS;
+  for (DOp& op : ops) op.flags &= ~kOpCS;
   for (const Seg& s : segs) {
+    if (s.kind == SEG_RLAYER && s.split == 1) {
+      for (int l = s.first; l < s.first + s.count; ++l) ops[l].flags |= kOpCS;
+      continue;
+    }
     if (s.kind != SEG_DIAG && s.kind != SEG_DIAGPERM) continue;
     const int nd = s.kind == SEG_DIAG ? s.count : s.split;
     for (int l = s.first; l < s.first + nd; ++l)
-      if (ops[l].type == SV_GATE_RZ) ops[l].flags |= kOpDiagCS;
+      if (ops[l].type == SV_GATE_RZ) ops[l].flags |= kOpCS;
   }
   return ckpt;
 }

@@ -37,9 +37,10 @@ sv_status lower_circuit(const sv_circuit* c, int expect_n, HostCircuit& out);
 // kMaxLayer CZ gates); a run of RY (or RX) gates on distinct qubits becomes SEG_RLAYER when it
 // holds at least `min_layer` gates (and at most kMaxLayer); a run of two to kMaxPerm CNOT/X
 // gates becomes SEG_PERM; a SEG_DIAG directly followed by a SEG_PERM becomes one
-// SEG_DIAGPERM; everything else is SEG_GATES.  The RZ gates of diagonal segments get the
-// kOpDiagCS flag (their coefficient is (cos, sin) instead of the lifting form).  Returns the
-// number of checkpoints used.
+// SEG_DIAGPERM; everything else is SEG_GATES.  A first SEG_RLAYER of RY gates is marked as a
+// product layer (split = 1, no checkpoint).  The RZ gates of diagonal segments and the gates
+// of a product layer get the kOpCS flag (their coefficient is (cos, sin) instead of the
+// lifting form).  Returns the number of checkpoints used.
 constexpr int kMaxLayer = 16;
 int segment_ops(std::vector<DOp>& ops, int min_layer, int min_diag_rz,
                 std::vector<Seg>& segs);

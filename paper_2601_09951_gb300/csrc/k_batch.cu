@@ -419,6 +419,41 @@ __device__ __forceinline__ GRec grec(const DGroup& G) {
   return r;
 }
 
+// A product layer (first segment: RY gates on the reference basis state |r>): the state it
+// makes is prod_b f_b(k_b), with f_b = (cos phi, sin phi) on bit values (0, 1) for a gate on a
+// bit with r_b = 0, (-sin phi, cos phi) for r_b = 1, and [k_b == r_b] on a bit without a gate.
+// The factors of bits [0, hl) and [hl, n) are multiplied out into the half tables tl and th
+// (real parts), so psi[k] = tl[k & lmask] * th[k >> hl].
+__device__ __noinline__ void product_setup(const Team& T, TeamS& S, const DOp* ops,
+                                           const Rot* coef, const Seg& sg, uint64_t ref, int n) {
+  if (T.rank < n) {
+    const bool r1 = (ref >> T.rank) & 1ull;
+    S.cs[T.rank] = r1 ? make_double2(0.0, 1.0) : make_double2(1.0, 0.0);
+  }
+  T.sync();
+  if (T.rank < sg.count) {
+    const int b = ops[sg.first + T.rank].bit0;
+    const Rot r = coef[sg.first + T.rank];  // (cos phi, sin phi)
+    const bool r1 = (ref >> b) & 1ull;
+    S.cs[b] = r1 ? make_double2(dneg(r.b), r.a) : make_double2(r.a, r.b);
+  }
+  T.sync();
+  const int hl = n < 6 ? n : 6;
+  const int nl = 1 << hl, nh = 1 << (n - hl);
+  for (int j = T.rank; j < nl + nh; j += T.size) {
+    const bool hi = j >= nl;
+    const int jj = hi ? j - nl : j;
+    const int b0 = hi ? hl : 0, b1 = hi ? n : hl;
+    double p = 1.0;
+    for (int b = b0; b < b1; ++b) {
+      const double2 f = S.cs[b];
+      p *= ((jj >> (b - b0)) & 1) ? f.y : f.x;
+    }
+    if (hi) S.th[jj] = make_double2(p, 0.0); else S.tl[jj] = make_double2(p, 0.0);
+  }
+  T.sync();
+}
+
 // Sign of the CZ gates of a diagonal segment at amplitude k (true = negative).
 __device__ __forceinline__ bool cz_sign(const TeamS& S, int ncz, uint32_t k) {
   uint32_t par = 0;
@@ -452,7 +487,7 @@ __device__ void run_instance(const BatchArgs& a, int idx, const Team& T, TeamS& 
   for (int step = 0; step < steps; ++step) {
     for (int g = tid; g < I.n_ops; g += TS) {
       const DOp op = ops[g];
-      if (op.flags & kOpDiagCS) {
+      if (op.flags & kOpCS) {
         const double t = op.param >= 0 ? theta[op.param] : op.fixed;
         Rot r;
         sincos(0.5 * t, &r.b, &r.a);
@@ -513,6 +548,11 @@ __device__ void run_instance(const BatchArgs& a, int idx, const Team& T, TeamS& 
           if (ncz && cz_sign(S, ncz, k)) v = make_double2(dneg(v.x), dneg(v.y));
           psi[k] = v;
         }
+        T.sync();
+      } else if (sg.kind == SEG_RLAYER && sg.split == 1) {
+        product_setup(T, S, ops, coef, sg, I.ref, n);
+        for (uint32_t k = tid; k < N; k += TS)
+          psi[k] = make_double2(S.tl[k & lmask].x * S.th[k >> hl].x, 0.0);
         T.sync();
       } else if (sg.kind == SEG_RLAYER) {
         // the layer's first pass also writes the checkpoint (a layer has at least two gates)
@@ -748,6 +788,10 @@ __device__ void run_instance(const BatchArgs& a, int idx, const Team& T, TeamS& 
         }
         const double tot = team_sum16(T, S, v, sg.count);
         if (tid < sg.count) contrib[sg.first + tid] = tot;
+        if (sg.split == 1) {  // a product layer: nothing before it needs psi or lambda
+          T.sync();
+          continue;
+        }
         // psi before the layer: the checkpoint copy runs while the layer is un-applied to
         // lambda (its gates commute: pairs in forward order, inverted), which leaves psi alone
         async_copy(T, psi, ck + (size_t)sg.ckpt * N, N);

@@ -18,16 +18,17 @@ struct DOp {
   int32_t k;       // number of inserted zero bits
   int32_t bit0;    // basis-index bit of the first wire (1-qubit gates)
   uint8_t sb[4];   // sorted bit positions of the wires
-  int32_t flags;   // kOpDiagCS: an RZ gate of a batched diagonal segment (see below)
+  int32_t flags;   // kOpCS: the batched kernel wants (cos, sin) for this op (see below)
   uint64_t lo_or;  // bits set in the first amplitude of each pair
   uint64_t flip;   // XOR mask from the first to the second amplitude
   double fixed;    // angle when param < 0
 };
 static_assert(sizeof(DOp) == 48, "DOp layout");
-// The batched kernel applies the RZ gates of a diagonal segment as one phase and needs their
-// (cos phi, sin phi), phi = theta/2, rather than the lifting form: for an op with this flag its
-// coefficient slot holds Rot{a = cos phi, b = sin phi, k = 0}.
-constexpr int32_t kOpDiagCS = 1;
+// The batched kernel needs (cos phi, sin phi), phi = theta/2, rather than the lifting form for
+// the RZ gates of a diagonal segment (applied as one phase) and for the RY gates of a
+// product-state layer: for an op with this flag its coefficient slot holds
+// Rot{a = cos phi, b = sin phi, k = 0}.
+constexpr int32_t kOpCS = 1;
 
 // Lifting form of the rotation R(phi) = [[c, -s], [s, c]] (phi = theta/2):
 // R(phi) = L(a) S(b) L(a) R(k pi/2), a = -tan(r/2), b = sin(r), r = phi - k pi/2 in
@@ -59,7 +60,10 @@ static_assert(sizeof(DGroup) == 32, "DGroup layout");
 //   SEG_RLAYER: RY (or RX) gates on distinct qubits.  They commute, so every gradient of the
 //               layer is taken from (psi, lambda) at the layer's end; the sweep then
 //               un-applies the layer to lambda only and reloads psi from a checkpoint saved
-//               on the forward pass.
+//               on the forward pass.  With split = 1 (the first segment, RY gates only) the
+//               layer acts on the reference basis state, so its output is a product state,
+//               written directly from two half tables; the sweep takes its gradients and stops
+//               there (no un-apply, no checkpoint).
 //   SEG_DIAG  : RZ and CZ gates (diagonal, mutually commuting), applied as one phase
 //               e^{-i sum_q phi_q s_q(k)} (+-1 for CZ) per amplitude from two half tables;
 //               gradients from w_k = Im(conj(lambda_k) psi_k); psi reloaded from a checkpoint.
@@ -75,7 +79,7 @@ static_assert(sizeof(DGroup) == 32, "DGroup layout");
 enum { SEG_GATES = 0, SEG_RLAYER = 1, SEG_DIAG = 2, SEG_PERM = 3, SEG_DIAGPERM = 4 };
 struct Seg {
   int16_t kind;
-  int16_t split;  // SEG_DIAGPERM: ops of the diagonal part; else 0
+  int16_t split;  // SEG_DIAGPERM: ops of the diagonal part; SEG_RLAYER: 1 = product layer
   int32_t first;  // first op
   int32_t count;  // number of ops
   int32_t ckpt;   // checkpoint slot of psi before the segment, or -1
