@@ -614,12 +614,24 @@ __device__ void run_instance(const BatchArgs& a, int idx, const Team& T, TeamS& 
             }
           }
         } else {
-          const bool full = zu == N - 1;
+          // table index pext(k, zu) with k = k0 + u TS (k0 < TS: N <= kHU TS in every class):
+          // the bits of zu below log_size give a per-thread base, and each set bit b of u adds
+          // d[b] (zero unless bit log_size + b is in zu)
+          const uint32_t zl = zu & (uint32_t)(TS - 1), zh = zu >> T.log_size;
+          const uint32_t base = pext32(k0, zl);
+          const int sh = __popc(zl);
+          uint32_t d[4];
+#pragma unroll
+          for (int b = 0; b < 4; ++b)
+            d[b] = ((zh >> b) & 1u) << (sh + __popc(zh & ((1u << b) - 1u)));
 #pragma unroll
           for (int u = 0; u < kHU; ++u) {
             const uint32_t k = k0 + u * TS;
             if (k < N) {
-              const uint32_t ti = full ? k : pext32(k, zu);
+              uint32_t ti = base;
+#pragma unroll
+              for (int b = 0; b < 4; ++b)
+                if ((u >> b) & 1) ti += d[b];
               group_madd(G.cls, a.tables[G.toff + ti], psi[k ^ x], acc[u]);
             }
           }
