@@ -46,6 +46,9 @@ def parse():
     ap.add_argument("--requests", type=int, default=300)
     ap.add_argument("--qubits", type=int, default=28)
     ap.add_argument("--ansatz", default="hea", choices=["hea", "uccsd"])
+    ap.add_argument("--checkpoint-gb", type=float, default=64.0,
+                    help="single: device memory for psi checkpoints of commuting layers "
+                         "(sv_set_checkpoint_bytes); 0 keeps psi and lambda only")
     return ap.parse_args()
 
 
@@ -348,6 +351,7 @@ def run_single(args):
     n = inst["circuit"]["n"]
     stream = torch.cuda.Stream()
     ctx = svqe.Context(n, stream=stream.cuda_stream)
+    ctx.set_checkpoint_bytes(int(args.checkpoint_gb * 2**30))
     ctx.init_reference(inst["ref"])
     H = svqe.Ham(ctx, inst["ham"])
     C = svqe.Circuit(inst["circuit"])
@@ -370,6 +374,7 @@ def run_single(args):
     print(json.dumps({"metric": "single-state energy+adjoint-gradient evals/s",
                       "workload": inst["name"], "n_qubits": n, "gates": len(C.gates),
                       "terms": len(inst["ham"]["coeff"]), "groups": H.info()[0],
+                      "checkpoint_bytes": int(args.checkpoint_gb * 2**30),
                       "ms_per_eval": ms, "value": 1e3 / ms, "unit": "evals/s",
                       "dtype": "f64"}), flush=True)
 

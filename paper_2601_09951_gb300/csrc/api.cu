@@ -45,6 +45,16 @@ struct sv_ctx {
   FItem* items = nullptr;     // fused-pass items of the staged circuit
   size_t items_cap = 0;
   HostPlan plan;              // fused passes of the staged circuit (empty: per-op kernels)
+  // psi checkpoints of commuting layers (sv_set_checkpoint_bytes): the staged circuit's fused
+  // passes are planned in chunks, each either a checkpointed layer or a run of other ops
+  uint64_t ck_budget = 0;
+  std::vector<double2*> ck;   // one state each
+  struct Chunk {
+    int first, count;  // ops
+    int ck;            // checkpoint buffer of a layer chunk, or -1
+    int p0, p1;        // passes [p0, p1) of plan
+  };
+  std::vector<Chunk> chunks;
 };
 
 struct sv_ham {
@@ -211,6 +221,7 @@ sv_status sv_destroy(sv_ctx* c) {
   cudaFree(c->grad);
   cudaFree(c->etraj);
   cudaFree(c->items);
+  for (double2* p : c->ck) cudaFree(p);
   if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
   cudaGetLastError();
   delete c;
@@ -357,8 +368,46 @@ sv_status svqe::stage_circuit(sv_ctx* c, const HostCircuit& hc) {
                             c->stream), c);
   c->plan.passes.clear();
   c->plan.items.clear();
+  c->chunks.clear();
   if (c->n >= kFusedMinQubits && n_ops > 0) {
-    plan_passes(hc.ops, c->n, fused_tile_bits(), c->plan);
+    // commuting layers that get a psi checkpoint: as many as the budget (and the device) allow
+    std::vector<std::pair<int, int>> layers = commuting_layers(hc.ops, 2);
+    const uint64_t sb = sv_state_bytes(c->n);
+    size_t n_ck = std::min<size_t>(layers.size(), (size_t)(c->ck_budget / sb));
+    while (c->ck.size() < n_ck) {
+      double2* buf = nullptr;
+      if (cudaMalloc((void**)&buf, sb) != cudaSuccess) {
+        cudaGetLastError();
+        break;
+      }
+      c->ck.push_back(buf);
+    }
+    n_ck = std::min(n_ck, c->ck.size());
+    layers.resize(n_ck);
+    auto plan_chunk = [&](int first, int count, int ckid) {
+      const std::vector<DOp> sub(hc.ops.begin() + first, hc.ops.begin() + first + count);
+      HostPlan sp;
+      plan_passes(sub, c->n, fused_tile_bits(), sp);
+      sv_ctx::Chunk ch{first, count, ckid, (int)c->plan.passes.size(), 0};
+      const int item0 = (int)c->plan.items.size();
+      for (FItem it : sp.items) {
+        it.op += first;
+        c->plan.items.push_back(it);
+      }
+      for (FPass P : sp.passes) {
+        P.first_item += item0;
+        c->plan.passes.push_back(P);
+      }
+      ch.p1 = (int)c->plan.passes.size();
+      c->chunks.push_back(ch);
+    };
+    int pos = 0;
+    for (size_t j = 0; j < layers.size(); ++j) {
+      if (layers[j].first > pos) plan_chunk(pos, layers[j].first - pos, -1);
+      plan_chunk(layers[j].first, layers[j].second, (int)j);
+      pos = layers[j].first + layers[j].second;
+    }
+    if (pos < (int)n_ops) plan_chunk(pos, (int)n_ops - pos, -1);
     SV_CUDA(grow(c->items, c->items_cap, c->plan.items.size()), c);
     SV_CUDA(cudaMemcpyAsync(c->items, c->plan.items.data(), c->plan.items.size() * sizeof(FItem),
                             cudaMemcpyHostToDevice, c->stream), c);
@@ -366,12 +415,19 @@ sv_status svqe::stage_circuit(sv_ctx* c, const HostCircuit& hc) {
   return SV_OK;
 }
 
-static sv_status forward(sv_ctx* c, const HostCircuit& hc, const double* theta_dev) {
+// save: copy psi into the checkpoint of every checkpointed layer before the layer runs.
+static sv_status forward(sv_ctx* c, const HostCircuit& hc, const double* theta_dev, bool save) {
   const int n_ops = (int)hc.ops.size();
   SV_CUDA(launch_prep_coefs(c->ops, n_ops, theta_dev, c->coef, c->stream), c);
   if (!c->plan.passes.empty()) {
-    for (const FPass& P : c->plan.passes)
-      SV_CUDA(launch_fpass(c->psi, P, c->items, c->ops, c->coef, theta_dev, c->stream), c);
+    for (const sv_ctx::Chunk& ch : c->chunks) {
+      if (save && ch.ck >= 0)
+        SV_CUDA(cudaMemcpyAsync(c->ck[ch.ck], c->psi, sv_state_bytes(c->n),
+                                cudaMemcpyDeviceToDevice, c->stream), c);
+      for (int p = ch.p0; p < ch.p1; ++p)
+        SV_CUDA(launch_fpass(c->psi, c->plan.passes[p], c->items, c->ops, c->coef, theta_dev,
+                             c->stream), c);
+    }
     return SV_OK;
   }
   for (int l = 0; l < n_ops; ++l)
@@ -384,16 +440,32 @@ static sv_status forward(sv_ctx* c, const HostCircuit& hc, const double* theta_d
 sv_status svqe::adjoint_core(sv_ctx* c, const HostCircuit& hc, const sv_ham* H,
                        const double* theta_dev, double* energy_dev, double* grad_dev) {
   SV_CUDA(launch_init_basis(c->psi, c->n, c->ref, c->stream), c);
-  sv_status st = forward(c, hc, theta_dev);
+  sv_status st = forward(c, hc, theta_dev, true);
   if (st != SV_OK) return st;
   SV_CUDA(launch_hpsi(c->psi, c->lam, c->n, H->groups, H->n_groups, H->tables, c->epart,
                       c->stream), c);
   SV_CUDA(launch_sum(c->epart, kRedBlocks, energy_dev, c->stream), c);
   const int n_ops = (int)hc.ops.size();
   if (!c->plan.passes.empty()) {
-    for (int p = (int)c->plan.passes.size() - 1; p >= 0; --p)
-      SV_CUDA(launch_bpass(c->psi, c->lam, c->plan.passes[p], c->items, c->ops, c->coef,
-                           theta_dev, c->gpart, c->stream), c);
+    for (int ci = (int)c->chunks.size() - 1; ci >= 0; --ci) {
+      const sv_ctx::Chunk& ch = c->chunks[ci];
+      if (ch.ck < 0) {
+        for (int p = ch.p1 - 1; p >= ch.p0; --p)
+          SV_CUDA(launch_bpass(c->psi, c->lam, c->plan.passes[p], c->items, c->ops, c->coef,
+                               theta_dev, c->gpart, c->stream), c);
+        continue;
+      }
+      // a checkpointed commuting layer: every gradient from (psi, lambda) at the layer's end,
+      // then the layer un-applied to lambda alone, and psi reloaded from the checkpoint
+      for (int p = ch.p0; p < ch.p1; ++p)
+        SV_CUDA(launch_gpass(c->psi, c->lam, c->plan.passes[p], c->items, c->ops, c->gpart,
+                             c->stream), c);
+      for (int p = ch.p1 - 1; p >= ch.p0; --p)
+        SV_CUDA(launch_fpass_inv(c->lam, c->plan.passes[p], c->items, c->ops, c->coef,
+                                 theta_dev, c->stream), c);
+      SV_CUDA(cudaMemcpyAsync(c->psi, c->ck[ch.ck], sv_state_bytes(c->n),
+                              cudaMemcpyDeviceToDevice, c->stream), c);
+    }
   } else {
     for (int l = n_ops - 1; l >= 0; --l) {
       const DOp& op = hc.ops[l];
@@ -418,7 +490,23 @@ sv_status sv_apply_circuit(sv_ctx* c, const sv_circuit* circ, const double* thet
   if (hc.n_params)
     SV_CUDA(cudaMemcpyAsync(c->theta, theta, hc.n_params * sizeof(double),
                             cudaMemcpyHostToDevice, c->stream), c);
-  return forward(c, hc, c->theta);
+  return forward(c, hc, c->theta, false);
+}
+
+sv_status sv_set_checkpoint_bytes(sv_ctx* c, uint64_t bytes) {
+  clear_error();
+  if (!c) { set_error("NULL handle"); return SV_EINVAL; }
+  SV_CHECK_STICKY(c);
+  c->ck_budget = bytes;
+  const size_t keep = (size_t)(bytes / sv_state_bytes(c->n));
+  if (c->ck.size() > keep) {
+    SV_CUDA(cudaStreamSynchronize(c->stream), c);
+    while (c->ck.size() > keep) {
+      cudaFree(c->ck.back());
+      c->ck.pop_back();
+    }
+  }
+  return SV_OK;
 }
 
 sv_status sv_expval_paulisum(sv_ctx* c, const sv_ham* H, double* energy_out) {

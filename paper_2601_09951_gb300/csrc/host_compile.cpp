@@ -219,6 +219,28 @@ int segment_ops(std::vector<DOp>& ops, int min_layer, int min_diag_rz,
   return ckpt;
 }
 
+std::vector<std::pair<int, int>> commuting_layers(const std::vector<DOp>& ops, int min_len) {
+  std::vector<std::pair<int, int>> out;
+  const int n_ops = (int)ops.size();
+  int l = 0;
+  while (l < n_ops) {
+    const int t = ops[l].type;
+    if (t != SV_GATE_RY && t != SV_GATE_RX) {
+      ++l;
+      continue;
+    }
+    uint64_t used = 0;
+    int e = l;
+    while (e < n_ops && ops[e].type == t && !(used & (1ull << ops[e].bit0))) {
+      used |= 1ull << ops[e].bit0;
+      ++e;
+    }
+    if (e - l >= min_len) out.push_back({l, e - l});
+    l = e;
+  }
+  return out;
+}
+
 namespace {
 struct Unit {      // a schedulable unit: one op, or a run of RZ ops (diagonal item)
   int kind;        // 0 op, 1 diag

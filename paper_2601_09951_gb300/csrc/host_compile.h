@@ -5,6 +5,7 @@
 #include <stdint.h>
 
 #include <string>
+#include <utility>
 #include <vector>
 
 #include "../../include/svqe.h"
@@ -44,6 +45,10 @@ sv_status lower_circuit(const sv_circuit* c, int expect_n, HostCircuit& out);
 constexpr int kMaxLayer = 16;
 int segment_ops(std::vector<DOp>& ops, int min_layer, int min_diag_rz,
                 std::vector<Seg>& segs);
+
+// Runs of RY (or RX) gates on distinct qubits with at least min_len gates, as (first, count):
+// the commuting layers whose gradients the single-state path can take at the layer's end.
+std::vector<std::pair<int, int>> commuting_layers(const std::vector<DOp>& ops, int min_len);
 
 // Plan the fused passes of an n-qubit circuit with tiles of m bits (see FPass): ops are taken
 // greedily in order into the current pass while the pass's pair bits fit the tile; an op may

@@ -219,6 +219,8 @@ __device__ __forceinline__ void tile_adj_k(double2* tp, double2* tl, uint32_t M,
   }
 }
 
+// INV: apply the pass's items inverted, in reverse order (un-applying the pass).
+template <bool INV>
 __global__ void __launch_bounds__(kFT) k_fpass(double2* __restrict__ psi, FPass P,
                                                const FItem* __restrict__ items,
                                                const DOp* __restrict__ gops,
@@ -240,10 +242,14 @@ __global__ void __launch_bounds__(kFT) k_fpass(double2* __restrict__ psi, FPass 
     for (uint32_t j = threadIdx.x; j < M; j += kFT) tile[j] = psi[gidx(hoff, j, P.c, outer)];
     if (diag >= 0) diag_tile(D, P, outer);
     __syncthreads();
-    for (int i = 0; i < P.n_items; ++i) {
+    for (int ii = 0; ii < P.n_items; ++ii) {
+      const int i = INV ? P.n_items - 1 - ii : ii;
       const FItem it = items[P.first_item + i];
       if (it.kind == 0) {
-        tile_op(tile, M, it.local, coef[it.op], false);
+        tile_op(tile, M, it.local, coef[it.op], INV);
+      } else if (INV) {
+        for (uint32_t j = threadIdx.x; j < M; j += kFT)
+          tile[j] = cmul_conj(tile[j], diag_phase(D, j));
       } else {
         for (uint32_t j = threadIdx.x; j < M; j += kFT) tile[j] = cmul(tile[j], diag_phase(D, j));
       }
@@ -366,6 +372,68 @@ __global__ void __launch_bounds__(kFT) k_bpass(double2* __restrict__ psi,
   }
 }
 
+// Gradients only: 2 Im<lambda|G|psi> of every parameterised single-op item of the pass from
+// the unchanged psi and lambda tiles (no un-apply, no stores).  Used for a commuting layer
+// whose gradients are all taken at the layer's end; the tiles are read-only, so the items need
+// no barrier between them.
+__global__ void __launch_bounds__(kFT) k_gpass(const double2* __restrict__ psi,
+                                               const double2* __restrict__ lam, FPass P,
+                                               const FItem* __restrict__ items,
+                                               double* __restrict__ partial) {
+  extern __shared__ double2 smem[];
+  __shared__ uint64_t hoff[1 << (11 - kMinLowBits)];
+  __shared__ double red[kFT / 32];
+  const uint32_t M = 1u << P.m;
+  double2* tp = smem;
+  double2* tlam = smem + M;
+  double* accp = (double*)(smem + 2 * M);  // [n_slots][kFT]
+  const uint64_t ntiles = 1ull << __popcll(P.outer_mask);
+  const int tid = threadIdx.x;
+  for (int s = 0; s < P.n_slots; ++s) accp[s * kFT + tid] = 0.0;
+  setup_hoff(hoff, P);
+  __syncthreads();
+  for (uint64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    const uint64_t outer = pdep64(t, P.outer_mask);
+    for (uint32_t j = tid; j < M; j += kFT) {
+      const uint64_t k = gidx(hoff, j, P.c, outer);
+      tp[j] = psi[k];
+      tlam[j] = lam[k];
+    }
+    __syncthreads();
+    for (int i = 0; i < P.n_items; ++i) {
+      const FItem it = items[P.first_item + i];
+      if (it.kind != 0 || it.slot < 0) continue;
+      const DOp& op = it.local;
+      const uint32_t np = M >> op.k;
+      const uint32_t lo = (uint32_t)op.lo_or, fl = (uint32_t)op.flip;
+      const int kind = fkind_of(op.type);
+      double acc = 0.0;
+      for (uint32_t p = tid; p < np; p += kFT) {
+        const uint32_t a = (uint32_t)insert_zeros(p, op.sb, op.k) | lo;
+        const double2 px = tp[a], py = tp[a ^ fl], lx = tlam[a], ly = tlam[a ^ fl];
+        if (kind == F_ROTX) fgrad<F_ROTX>(lx, ly, px, py, acc);
+        else if (kind == F_ROTZ) fgrad<F_ROTZ>(lx, ly, px, py, acc);
+        else fgrad<F_ROTY>(lx, ly, px, py, acc);
+      }
+      accp[it.slot * kFT + tid] += acc;
+    }
+    __syncthreads();
+  }
+  for (int i = 0; i < P.n_items; ++i) {
+    const FItem it = items[P.first_item + i];
+    if (it.kind != 0 || it.slot < 0) continue;
+    double v = warp_sum(accp[it.slot * kFT + tid]);
+    if ((tid & 31) == 0) red[tid >> 5] = v;
+    __syncthreads();
+    if (tid < 32) {
+      double u = tid < kFT / 32 ? red[tid] : 0.0;
+      u = warp_sum(u);
+      if (tid == 0) partial[(size_t)it.op * kRedBlocks + blockIdx.x] = u;
+    }
+    __syncthreads();
+  }
+}
+
 }  // namespace
 
 int fused_tile_bits() { return 11; }
@@ -376,8 +444,14 @@ size_t bpass_smem(int m, int slots) {
 }
 
 cudaError_t fused_prepare() {
-  cudaError_t e = cudaFuncSetAttribute(k_fpass, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  cudaError_t e = cudaFuncSetAttribute(k_fpass<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)fpass_smem(12));
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(k_fpass<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)fpass_smem(12));
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(k_gpass, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)bpass_smem(11, kMaxSlotsDev));
   if (e != cudaSuccess) return e;
   return cudaFuncSetAttribute(k_bpass, cudaFuncAttributeMaxDynamicSharedMemorySize,
                               (int)bpass_smem(11, kMaxSlotsDev));
@@ -387,7 +461,22 @@ cudaError_t launch_fpass(double2* psi, const FPass& P, const FItem* items, const
                          const Rot* coef, const double* theta, cudaStream_t s) {
   const uint64_t ntiles = 1ull << __builtin_popcountll(P.outer_mask);
   const int grid = (int)std::min<uint64_t>(ntiles, kRedBlocks);
-  k_fpass<<<grid, kFT, fpass_smem(P.m), s>>>(psi, P, items, gops, coef, theta);
+  k_fpass<false><<<grid, kFT, fpass_smem(P.m), s>>>(psi, P, items, gops, coef, theta);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_fpass_inv(double2* v, const FPass& P, const FItem* items, const DOp* gops,
+                             const Rot* coef, const double* theta, cudaStream_t s) {
+  const uint64_t ntiles = 1ull << __builtin_popcountll(P.outer_mask);
+  const int grid = (int)std::min<uint64_t>(ntiles, kRedBlocks);
+  k_fpass<true><<<grid, kFT, fpass_smem(P.m), s>>>(v, P, items, gops, coef, theta);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_gpass(const double2* psi, const double2* lam, const FPass& P,
+                         const FItem* items, const DOp* gops, double* partial, cudaStream_t s) {
+  (void)gops;
+  k_gpass<<<kRedBlocks, kFT, bpass_smem(P.m, P.n_slots), s>>>(psi, lam, P, items, partial);
   return cudaGetLastError();
 }
 

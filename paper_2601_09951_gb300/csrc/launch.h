@@ -45,6 +45,13 @@ int fused_tile_bits();
 cudaError_t fused_prepare();
 cudaError_t launch_fpass(double2* psi, const FPass& P, const FItem* items, const DOp* gops,
                          const Rot* coef, const double* theta, cudaStream_t s);
+// The pass's items inverted and in reverse order, on v (un-applying the pass).
+cudaError_t launch_fpass_inv(double2* v, const FPass& P, const FItem* items, const DOp* gops,
+                             const Rot* coef, const double* theta, cudaStream_t s);
+// Gradient shares only (psi and lambda unchanged) of a pass whose items are single ops:
+// partial[op * kRedBlocks + b] as for launch_bpass.
+cudaError_t launch_gpass(const double2* psi, const double2* lam, const FPass& P,
+                         const FItem* items, const DOp* gops, double* partial, cudaStream_t s);
 // Backward pass: partial[op * kRedBlocks + b] receives block b's gradient share of every
 // parameterised op of the pass.
 cudaError_t launch_bpass(double2* psi, double2* lam, const FPass& P, const FItem* items,

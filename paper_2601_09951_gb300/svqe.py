@@ -72,6 +72,7 @@ def lib():
         "sv_ctx_device_bytes": ([i32], u64),
         "sv_create": ([P, i32, P], i32),
         "sv_destroy": ([P], i32),
+        "sv_set_checkpoint_bytes": ([P, u64], i32),
         "sv_ham_upload": ([P, P, P], i32),
         "sv_ham_free": ([P], i32),
         "sv_ham_info": ([P, P, P], i32),
@@ -307,6 +308,10 @@ class Context:
         out = np.empty(1 << self.n, dtype=np.complex128)
         _check(lib().sv_get_state(self._c, _ptr(out)))
         return out
+
+    def set_checkpoint_bytes(self, nbytes):
+        """Device memory for psi checkpoints of commuting layers (sv_set_checkpoint_bytes)."""
+        _check(lib().sv_set_checkpoint_bytes(self._c, int(nbytes)))
 
     def set_state(self, psi):
         a = np.ascontiguousarray(psi, dtype=np.complex128)

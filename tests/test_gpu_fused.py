@@ -106,3 +106,36 @@ def test_fused_and_per_op_paths_agree_on_the_state():
                "n_params": circ["n_params"]}
         ctx.apply_circuit(one, inst["theta"])
     np.testing.assert_allclose(ctx.get_state(), fused, atol=PSI_TOL)
+
+
+@pytest.mark.parametrize("make,budget_layers", [
+    (lambda: W.hea_instance(16, 3, 60, 35, ring=True), 3),
+    (lambda: W.hea_instance(14, 4, 80, 36), 2),
+    (lambda: W.hea_instance(15, 2, 50, 37), 8),
+])
+def test_checkpointed_layers_match_oracle_and_plain_sweep(make, budget_layers):
+    """With a checkpoint budget, commuting RY layers take their gradients at the layer's end and
+    the sweep un-applies them to lambda only, reloading psi.  Energy and gradient match the
+    oracle and the sweep without checkpoints, and psi returns to the reference state."""
+    inst = make()
+    n = inst["circuit"]["n"]
+    ctx = svqe.Context(n)
+    ctx.init_reference(inst["ref"])
+    H = svqe.Ham(ctx, inst["ham"])
+    e_plain, g_plain = ctx.adjoint_grad(inst["circuit"], inst["theta"], H)
+    ctx.set_checkpoint_bytes(budget_layers * svqe.state_bytes(n))
+    e, g = ctx.adjoint_grad(inst["circuit"], inst["theta"], H)
+    e0, g0 = oracle.energy_grad(inst)
+    assert_energy(e, e0, inst["ham"], inst["name"])
+    assert_grad(g, g0, inst["ham"], inst["name"])
+    assert abs(e - e_plain) <= 1e-13 * max(1.0, abs(e_plain))
+    np.testing.assert_allclose(g, g_plain, rtol=0, atol=1e-11 * max(1.0, np.abs(g_plain).max()))
+    ref = np.zeros(1 << n, np.complex128)
+    ref[inst["ref"]] = 1.0
+    assert np.max(np.abs(ctx.get_state() - ref)) <= 1e-12
+    # a second call with the same buffers, then the budget withdrawn
+    e2, g2 = ctx.adjoint_grad(inst["circuit"], inst["theta"], H)
+    assert e2 == e and np.array_equal(g2, g)
+    ctx.set_checkpoint_bytes(0)
+    e3, g3 = ctx.adjoint_grad(inst["circuit"], inst["theta"], H)
+    assert e3 == e_plain and np.array_equal(g3, g_plain)
