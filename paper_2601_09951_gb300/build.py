@@ -14,7 +14,8 @@ CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "libsvqe.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["api.cu", "k_state.cu", "k_batch.cu", "k_fused.cu", "noalloc.cu", "serve.cu", "host_compile.cpp"]
+SOURCES = ["api.cu", "k_state.cu", "k_batch.cu", "k_fused.cu", "k_dp.cu", "noalloc.cu", "serve.cu",
+           "host_compile.cpp"]
 
 
 def _nvcc():

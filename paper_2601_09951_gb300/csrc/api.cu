@@ -49,10 +49,20 @@ struct sv_ctx {
   // passes are planned in chunks, each either a checkpointed layer or a run of other ops
   uint64_t ck_budget = 0;
   std::vector<double2*> ck;   // one state each
+  // whole-state diagonal + permutation segments (k_dp.cu) need a third state buffer
+  double2* scratch = nullptr;
+  bool scratch_failed = false;
+  uint32_t* dp_tab = nullptr;   // permutation tables of the staged segments
+  size_t dp_tab_cap = 0;
+  double2* dp_phase = nullptr;  // their phase tables (written from theta every evaluation)
+  size_t dp_phase_cap = 0;
+  enum { CH_PASSES = 0, CH_LAYER = 1, CH_DP = 2 };
   struct Chunk {
+    int kind;
     int first, count;  // ops
-    int ck;            // checkpoint buffer of a layer chunk, or -1
-    int p0, p1;        // passes [p0, p1) of plan
+    int ck;            // CH_LAYER: its checkpoint buffer
+    int p0, p1;        // CH_PASSES / CH_LAYER: passes [p0, p1) of plan
+    DpArgs dp;         // CH_DP
   };
   std::vector<Chunk> chunks;
 };
@@ -196,7 +206,8 @@ sv_status sv_create(sv_ctx** out, int32_t n, void* stream) {
     return SV_ENOMEM;
   }
   c->ref = 0;
-  if (fused_prepare() != cudaSuccess || launch_init_basis(c->psi, n, 0, c->stream) != cudaSuccess) {
+  if (fused_prepare() != cudaSuccess || dp_prepare() != cudaSuccess ||
+      launch_init_basis(c->psi, n, 0, c->stream) != cudaSuccess) {
     set_error("init kernel launch failed");
     sv_destroy(c);
     return SV_ECUDA;
@@ -222,6 +233,9 @@ sv_status sv_destroy(sv_ctx* c) {
   cudaFree(c->etraj);
   cudaFree(c->items);
   for (double2* p : c->ck) cudaFree(p);
+  cudaFree(c->scratch);
+  cudaFree(c->dp_tab);
+  cudaFree(c->dp_phase);
   if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
   cudaGetLastError();
   delete c;
@@ -384,11 +398,47 @@ sv_status svqe::stage_circuit(sv_ctx* c, const HostCircuit& hc) {
     }
     n_ck = std::min(n_ck, c->ck.size());
     layers.resize(n_ck);
-    auto plan_chunk = [&](int first, int count, int ckid) {
+    std::vector<int> layer_at(n_ops, -1);
+    for (size_t j = 0; j < layers.size(); ++j) layer_at[layers[j].first] = (int)j;
+    // diagonal + permutation runs need the third buffer
+    if (!c->scratch && !c->scratch_failed) {
+      if (cudaMalloc((void**)&c->scratch, sb) != cudaSuccess) {
+        cudaGetLastError();
+        c->scratch = nullptr;
+        c->scratch_failed = true;
+      }
+    }
+    const bool use_dp = c->scratch != nullptr;
+    std::vector<uint32_t> tabs;
+    auto is_diag = [&](int t) { return t == SV_GATE_RZ || t == SV_GATE_CZ; };
+    auto is_perm = [&](int t) { return t == SV_GATE_CNOT || t == SV_GATE_X; };
+    // a run of RZ/CZ (at most kDpMaxRz / kDpMaxCz) then at least two CNOT/X gates, from l
+    auto dp_at = [&](int l, int& split, int& len) -> bool {
+      int d = l, nrz = 0, ncz = 0;
+      while (d < (int)n_ops && is_diag(hc.ops[d].type) &&
+             nrz + (hc.ops[d].type == SV_GATE_RZ) <= kDpMaxRz &&
+             ncz + (hc.ops[d].type == SV_GATE_CZ) <= kDpMaxCz) {
+        nrz += hc.ops[d].type == SV_GATE_RZ;
+        ncz += hc.ops[d].type == SV_GATE_CZ;
+        ++d;
+      }
+      int e = d;
+      while (e < (int)n_ops && is_perm(hc.ops[e].type)) ++e;
+      if (e - d < 2) return false;
+      split = d - l;
+      len = e - l;
+      return true;
+    };
+    auto plan_chunk = [&](int kind, int first, int count, int ckid) {
       const std::vector<DOp> sub(hc.ops.begin() + first, hc.ops.begin() + first + count);
       HostPlan sp;
       plan_passes(sub, c->n, fused_tile_bits(), sp);
-      sv_ctx::Chunk ch{first, count, ckid, (int)c->plan.passes.size(), 0};
+      sv_ctx::Chunk ch{};
+      ch.kind = kind;
+      ch.first = first;
+      ch.count = count;
+      ch.ck = ckid;
+      ch.p0 = (int)c->plan.passes.size();
       const int item0 = (int)c->plan.items.size();
       for (FItem it : sp.items) {
         it.op += first;
@@ -401,33 +451,127 @@ sv_status svqe::stage_circuit(sv_ctx* c, const HostCircuit& hc) {
       ch.p1 = (int)c->plan.passes.size();
       c->chunks.push_back(ch);
     };
-    int pos = 0;
-    for (size_t j = 0; j < layers.size(); ++j) {
-      if (layers[j].first > pos) plan_chunk(pos, layers[j].first - pos, -1);
-      plan_chunk(layers[j].first, layers[j].second, (int)j);
-      pos = layers[j].first + layers[j].second;
+    auto dp_chunk = [&](int first, int split, int len) {
+      sv_ctx::Chunk ch{};
+      ch.kind = sv_ctx::CH_DP;
+      ch.first = first;
+      ch.count = len;
+      ch.ck = (int)(tabs.size() / kDpTableWords);  // index of the segment's tables
+      DpArgs& d = ch.dp;
+      d.n = c->n;
+      d.N = c->N;
+      for (int l = first; l < first + split; ++l) {
+        const DOp& op = hc.ops[l];
+        if (op.type == SV_GATE_RZ) {
+          d.rz_all[d.n_rz_all++] = l;
+          if (op.param >= 0) {
+            d.rz_op[d.n_rz] = l;
+            d.rz_bit[d.n_rz] = op.bit0;
+            ++d.n_rz;
+          }
+        } else {
+          d.cz_mask[d.n_cz++] = (uint32_t)op.lo_or;
+        }
+      }
+      // P(k): the CNOT/X gates' conditional flips in order; tables over bits [0, 11),
+      // [11, 22), [22, 31), the first holding P(0)
+      auto P = [&](uint32_t k) {
+        for (int l = first + split; l < first + len; ++l) {
+          const uint32_t lo = (uint32_t)hc.ops[l].lo_or, fl = (uint32_t)hc.ops[l].flip;
+          if ((k & lo) == lo) k ^= fl;
+        }
+        return k;
+      };
+      const uint32_t c0 = P(0);
+      for (int t = 0; t < 3; ++t)
+        for (uint32_t j = 0; j < 2048; ++j) {
+          const uint64_t k = (uint64_t)j << (11 * t);
+          tabs.push_back(k < c->N ? (t == 0 ? P((uint32_t)k) : P((uint32_t)k) ^ c0) : 0u);
+        }
+      c->chunks.push_back(ch);
+    };
+    int i = 0, pass_start = 0;
+    auto flush = [&](int end) {
+      if (end > pass_start) plan_chunk(sv_ctx::CH_PASSES, pass_start, end - pass_start, -1);
+    };
+    while (i < (int)n_ops) {
+      int split = 0, len = 0;
+      if (layer_at[i] >= 0) {
+        flush(i);
+        const int j = layer_at[i];
+        plan_chunk(sv_ctx::CH_LAYER, layers[j].first, layers[j].second, j);
+        i += layers[j].second;
+        pass_start = i;
+      } else if (use_dp && (i == 0 || !is_diag(hc.ops[i - 1].type) || i == pass_start) &&
+                 dp_at(i, split, len)) {
+        flush(i);
+        dp_chunk(i, split, len);
+        i += len;
+        pass_start = i;
+      } else {
+        ++i;
+      }
     }
-    if (pos < (int)n_ops) plan_chunk(pos, (int)n_ops - pos, -1);
-    SV_CUDA(grow(c->items, c->items_cap, c->plan.items.size()), c);
-    SV_CUDA(cudaMemcpyAsync(c->items, c->plan.items.data(), c->plan.items.size() * sizeof(FItem),
-                            cudaMemcpyHostToDevice, c->stream), c);
+    flush((int)n_ops);
+    SV_CUDA(grow(c->items, c->items_cap, std::max<size_t>(1, c->plan.items.size())), c);
+    if (!c->plan.items.empty())
+      SV_CUDA(cudaMemcpyAsync(c->items, c->plan.items.data(),
+                              c->plan.items.size() * sizeof(FItem), cudaMemcpyHostToDevice,
+                              c->stream), c);
+    const size_t n_dp = tabs.size() / kDpTableWords;
+    if (n_dp) {
+      SV_CUDA(grow(c->dp_tab, c->dp_tab_cap, tabs.size()), c);
+      SV_CUDA(grow(c->dp_phase, c->dp_phase_cap, n_dp * kDpPhaseEntries), c);
+      SV_CUDA(cudaMemcpyAsync(c->dp_tab, tabs.data(), tabs.size() * sizeof(uint32_t),
+                              cudaMemcpyHostToDevice, c->stream), c);
+      for (sv_ctx::Chunk& ch : c->chunks) {
+        if (ch.kind != sv_ctx::CH_DP) continue;
+        DpArgs& d = ch.dp;
+        double2* ph = c->dp_phase + (size_t)ch.ck * kDpPhaseEntries;
+        d.perm = c->dp_tab + (size_t)ch.ck * kDpTableWords;
+        d.phase_lo = d.phase_lo_w = ph;
+        d.phase_b1 = d.phase_b1_w = ph + 2048;
+        d.phase_b2 = d.phase_b2_w = ph + 3072;
+      }
+    }
   }
   return SV_OK;
 }
 
-// save: copy psi into the checkpoint of every checkpointed layer before the layer runs.
-static sv_status forward(sv_ctx* c, const HostCircuit& hc, const double* theta_dev, bool save) {
+// The state buffers a whole-state segment may write: psi, lambda and the scratch buffer.
+static double2* free_buffer(sv_ctx* c, const double2* a, const double2* b) {
+  double2* pool[3] = {c->lam, c->scratch, c->psi};
+  for (double2* p : pool)
+    if (p && p != a && p != b) return p;
+  return nullptr;
+}
+
+// Forward pass of the staged circuit.  With chunks, psi may end in another state buffer
+// (whole-state segments are out of place): *psi_out receives where it is.  save: copy psi
+// into the checkpoint of every checkpointed layer before the layer runs.
+static sv_status forward(sv_ctx* c, const HostCircuit& hc, const double* theta_dev, bool save,
+                         double2** psi_out) {
   const int n_ops = (int)hc.ops.size();
+  *psi_out = c->psi;
   SV_CUDA(launch_prep_coefs(c->ops, n_ops, theta_dev, c->coef, c->stream), c);
-  if (!c->plan.passes.empty()) {
+  if (!c->chunks.empty()) {
+    double2* psi = c->psi;
     for (const sv_ctx::Chunk& ch : c->chunks) {
-      if (save && ch.ck >= 0)
-        SV_CUDA(cudaMemcpyAsync(c->ck[ch.ck], c->psi, sv_state_bytes(c->n),
+      if (ch.kind == sv_ctx::CH_DP) {
+        double2* dst = free_buffer(c, psi, nullptr);
+        SV_CUDA(launch_dp_setup(ch.dp, c->ops, theta_dev, c->stream), c);
+        SV_CUDA(launch_dp_fwd(psi, dst, ch.dp, c->stream), c);
+        psi = dst;
+        continue;
+      }
+      if (save && ch.kind == sv_ctx::CH_LAYER)
+        SV_CUDA(cudaMemcpyAsync(c->ck[ch.ck], psi, sv_state_bytes(c->n),
                                 cudaMemcpyDeviceToDevice, c->stream), c);
       for (int p = ch.p0; p < ch.p1; ++p)
-        SV_CUDA(launch_fpass(c->psi, c->plan.passes[p], c->items, c->ops, c->coef, theta_dev,
+        SV_CUDA(launch_fpass(psi, c->plan.passes[p], c->items, c->ops, c->coef, theta_dev,
                              c->stream), c);
     }
+    *psi_out = psi;
     return SV_OK;
   }
   for (int l = 0; l < n_ops; ++l)
@@ -440,32 +584,47 @@ static sv_status forward(sv_ctx* c, const HostCircuit& hc, const double* theta_d
 sv_status svqe::adjoint_core(sv_ctx* c, const HostCircuit& hc, const sv_ham* H,
                        const double* theta_dev, double* energy_dev, double* grad_dev) {
   SV_CUDA(launch_init_basis(c->psi, c->n, c->ref, c->stream), c);
-  sv_status st = forward(c, hc, theta_dev, true);
+  double2* psi = nullptr;
+  sv_status st = forward(c, hc, theta_dev, true, &psi);
   if (st != SV_OK) return st;
-  SV_CUDA(launch_hpsi(c->psi, c->lam, c->n, H->groups, H->n_groups, H->tables, c->epart,
+  double2* lam = psi == c->lam ? c->psi : c->lam;
+  SV_CUDA(launch_hpsi(psi, lam, c->n, H->groups, H->n_groups, H->tables, c->epart,
                       c->stream), c);
   SV_CUDA(launch_sum(c->epart, kRedBlocks, energy_dev, c->stream), c);
   const int n_ops = (int)hc.ops.size();
-  if (!c->plan.passes.empty()) {
+  if (!c->chunks.empty()) {
     for (int ci = (int)c->chunks.size() - 1; ci >= 0; --ci) {
       const sv_ctx::Chunk& ch = c->chunks[ci];
-      if (ch.ck < 0) {
+      if (ch.kind == sv_ctx::CH_PASSES) {
         for (int p = ch.p1 - 1; p >= ch.p0; --p)
-          SV_CUDA(launch_bpass(c->psi, c->lam, c->plan.passes[p], c->items, c->ops, c->coef,
+          SV_CUDA(launch_bpass(psi, lam, c->plan.passes[p], c->items, c->ops, c->coef,
                                theta_dev, c->gpart, c->stream), c);
-        continue;
+      } else if (ch.kind == sv_ctx::CH_LAYER) {
+        // a checkpointed commuting layer: every gradient from (psi, lambda) at the layer's
+        // end, then the layer un-applied to lambda alone; psi before the layer is the
+        // checkpoint itself (the buffer is not needed again in this sweep)
+        for (int p = ch.p0; p < ch.p1; ++p)
+          SV_CUDA(launch_gpass(psi, lam, c->plan.passes[p], c->items, c->ops, c->gpart,
+                               c->stream), c);
+        for (int p = ch.p1 - 1; p >= ch.p0; --p)
+          SV_CUDA(launch_fpass_inv(lam, c->plan.passes[p], c->items, c->ops, c->coef,
+                                   theta_dev, c->stream), c);
+        psi = c->ck[ch.ck];
+      } else {
+        // diagonal + permutation: psi gathered and un-phased into a free buffer, then lambda
+        // likewise with the RZ gradients from the two un-phased states
+        double2* psi_b = free_buffer(c, psi, lam);
+        SV_CUDA(launch_dp_bwd_psi(psi, psi_b, ch.dp, c->stream), c);
+        double2* lam_b = free_buffer(c, psi_b, lam);
+        SV_CUDA(launch_dp_bwd_lam(lam, psi_b, lam_b, ch.dp, c->gpart, c->stream), c);
+        psi = psi_b;
+        lam = lam_b;
       }
-      // a checkpointed commuting layer: every gradient from (psi, lambda) at the layer's end,
-      // then the layer un-applied to lambda alone, and psi reloaded from the checkpoint
-      for (int p = ch.p0; p < ch.p1; ++p)
-        SV_CUDA(launch_gpass(c->psi, c->lam, c->plan.passes[p], c->items, c->ops, c->gpart,
-                             c->stream), c);
-      for (int p = ch.p1 - 1; p >= ch.p0; --p)
-        SV_CUDA(launch_fpass_inv(c->lam, c->plan.passes[p], c->items, c->ops, c->coef,
-                                 theta_dev, c->stream), c);
-      SV_CUDA(cudaMemcpyAsync(c->psi, c->ck[ch.ck], sv_state_bytes(c->n),
-                              cudaMemcpyDeviceToDevice, c->stream), c);
     }
+    // psi is back at the reference state; it lives in the context's psi buffer between calls
+    if (psi != c->psi)
+      SV_CUDA(cudaMemcpyAsync(c->psi, psi, sv_state_bytes(c->n), cudaMemcpyDeviceToDevice,
+                              c->stream), c);
   } else {
     for (int l = n_ops - 1; l >= 0; --l) {
       const DOp& op = hc.ops[l];
@@ -490,7 +649,12 @@ sv_status sv_apply_circuit(sv_ctx* c, const sv_circuit* circ, const double* thet
   if (hc.n_params)
     SV_CUDA(cudaMemcpyAsync(c->theta, theta, hc.n_params * sizeof(double),
                             cudaMemcpyHostToDevice, c->stream), c);
-  return forward(c, hc, c->theta, false);
+  double2* psi = nullptr;
+  if ((st = forward(c, hc, c->theta, false, &psi)) != SV_OK) return st;
+  if (psi != c->psi)
+    SV_CUDA(cudaMemcpyAsync(c->psi, psi, sv_state_bytes(c->n), cudaMemcpyDeviceToDevice,
+                            c->stream), c);
+  return SV_OK;
 }
 
 sv_status sv_set_checkpoint_bytes(sv_ctx* c, uint64_t bytes) {

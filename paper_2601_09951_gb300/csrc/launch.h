@@ -48,6 +48,45 @@ cudaError_t launch_fpass(double2* psi, const FPass& P, const FItem* items, const
 // The pass's items inverted and in reverse order, on v (un-applying the pass).
 cudaError_t launch_fpass_inv(double2* v, const FPass& P, const FItem* items, const DOp* gops,
                              const Rot* coef, const double* theta, cudaStream_t s);
+// Whole-state diagonal + permutation segment of the single-state path (k_dp.cu): a run of
+// RZ/CZ gates followed by a run of CNOT/X gates, applied in one out-of-place streaming pass
+// for n >= 14.  perm: the permutation P of the CNOT/X run (gates in order) as three
+// 2048-entry tables over index bits [0, 11), [11, 22), [22, 31) (the first including P(0));
+// phase tables (written by launch_dp_setup from theta): e^{-i sum phi s(k)} of
+// the RZ gates over the 11 low bits, and over block-index bits [0, 10) and [10, 20).
+constexpr int kDpMaxRz = 32;
+constexpr int kDpMaxCz = 16;
+struct DpArgs {
+  uint64_t N;
+  int n;
+  const uint32_t* perm;
+  const double2* phase_lo;
+  const double2* phase_b1;
+  const double2* phase_b2;
+  double2* phase_lo_w;
+  double2* phase_b1_w;
+  double2* phase_b2_w;
+  int n_cz;
+  uint32_t cz_mask[kDpMaxCz];
+  int n_rz;                  // parameterised RZ ops: gradient targets
+  int rz_op[kDpMaxRz];
+  int rz_bit[kDpMaxRz];
+  int n_rz_all;              // every RZ op of the diagonal part: phase factors
+  int rz_all[kDpMaxRz];
+};
+constexpr size_t kDpTableWords = 3 * 2048;     // uint32 per permutation
+constexpr size_t kDpPhaseEntries = 2048 + 2048;  // double2 per segment (low + two block tables)
+cudaError_t dp_prepare();
+cudaError_t launch_dp_setup(const DpArgs& a, const DOp* ops, const double* theta, cudaStream_t s);
+// out[P(k)] = phase(k) in[k]
+cudaError_t launch_dp_fwd(const double2* in, double2* out, const DpArgs& a, cudaStream_t s);
+// out[k] = conj(phase(k)) in[P(k)]
+cudaError_t launch_dp_bwd_psi(const double2* in, double2* out, const DpArgs& a, cudaStream_t s);
+// out[k] = conj(phase(k)) lam[P(k)]; RZ gradient shares from w_k = Im(conj(out[k]) psi_b[k])
+// into partial[op * kRedBlocks + block]
+cudaError_t launch_dp_bwd_lam(const double2* lam, const double2* psi_b, double2* out,
+                              const DpArgs& a, double* partial, cudaStream_t s);
+
 // Gradient shares only (psi and lambda unchanged) of a pass whose items are single ops:
 // partial[op * kRedBlocks + b] as for launch_bpass.
 cudaError_t launch_gpass(const double2* psi, const double2* lam, const FPass& P,
