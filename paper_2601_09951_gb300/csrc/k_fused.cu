@@ -97,6 +97,17 @@ __device__ __forceinline__ double2 diag_phase(const DiagS& D, uint32_t j) {
   return cmul(D.th[j >> D.hl], D.tl[j & ((1u << D.hl) - 1u)]);
 }
 
+// Asynchronous 16-byte global -> shared copies (cp.async, L2 only): a tile's loads are all in
+// flight at once instead of one round trip per loop iteration; cp_async_wait_all and a
+// barrier complete them.
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+  const uint32_t d = (uint32_t)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() {
+  asm volatile("cp.async.wait_all;" ::: "memory");
+}
+
 // Tile-local index j -> global amplitude index.
 __device__ __forceinline__ uint64_t gidx(const uint64_t* hoff, uint32_t j, int c,
                                          uint64_t outer) {
@@ -239,7 +250,9 @@ __global__ void __launch_bounds__(kFT) k_fpass(double2* __restrict__ psi, FPass 
   __syncthreads();
   for (uint64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
     const uint64_t outer = pdep64(t, P.outer_mask);
-    for (uint32_t j = threadIdx.x; j < M; j += kFT) tile[j] = psi[gidx(hoff, j, P.c, outer)];
+    for (uint32_t j = threadIdx.x; j < M; j += kFT)
+      cp_async16(&tile[j], &psi[gidx(hoff, j, P.c, outer)]);
+    cp_async_wait_all();
     if (diag >= 0) diag_tile(D, P, outer);
     __syncthreads();
     for (int ii = 0; ii < P.n_items; ++ii) {
@@ -288,9 +301,10 @@ __global__ void __launch_bounds__(kFT) k_bpass(double2* __restrict__ psi,
     const uint64_t outer = pdep64(t, P.outer_mask);
     for (uint32_t j = tid; j < M; j += kFT) {
       const uint64_t k = gidx(hoff, j, P.c, outer);
-      tp[j] = psi[k];
-      tlam[j] = lam[k];
+      cp_async16(&tp[j], &psi[k]);
+      cp_async16(&tlam[j], &lam[k]);
     }
+    cp_async_wait_all();
     if (diag >= 0) diag_tile(D, P, outer);
     __syncthreads();
     for (int i = P.n_items - 1; i >= 0; --i) {
@@ -396,9 +410,10 @@ __global__ void __launch_bounds__(kFT) k_gpass(const double2* __restrict__ psi,
     const uint64_t outer = pdep64(t, P.outer_mask);
     for (uint32_t j = tid; j < M; j += kFT) {
       const uint64_t k = gidx(hoff, j, P.c, outer);
-      tp[j] = psi[k];
-      tlam[j] = lam[k];
+      cp_async16(&tp[j], &psi[k]);
+      cp_async16(&tlam[j], &lam[k]);
     }
+    cp_async_wait_all();
     __syncthreads();
     for (int i = 0; i < P.n_items; ++i) {
       const FItem it = items[P.first_item + i];
