@@ -593,6 +593,9 @@ sv_status svqe::adjoint_core(sv_ctx* c, const HostCircuit& hc, const sv_ham* H,
   SV_CUDA(launch_sum(c->epart, kRedBlocks, energy_dev, c->stream), c);
   const int n_ops = (int)hc.ops.size();
   if (!c->chunks.empty()) {
+    // passes over fewer tiles than kRedBlocks launch fewer blocks: their other partials are 0
+    SV_CUDA(cudaMemsetAsync(c->gpart, 0, (size_t)std::max(1, n_ops) * kRedBlocks * sizeof(double),
+                            c->stream), c);
     for (int ci = (int)c->chunks.size() - 1; ci >= 0; --ci) {
       const sv_ctx::Chunk& ch = c->chunks[ci];
       if (ch.kind == sv_ctx::CH_PASSES) {

@@ -6,7 +6,9 @@
 // Backward: k_bpass stages psi and lambda, walks the items in reverse, accumulates each
 //           parameterised item's 2 Im<lambda|G|psi> in a per-thread shared-memory slot (one
 //           DADD per item per tile instead of a warp reduction), un-applies the items to both,
-//           and reduces every slot once at the end into partial[op * kRedBlocks + block].
+//           and reduces every slot once at the end into partial[op * kRedBlocks + block] (one
+//           block per tile up to kRedBlocks; the caller zeroes the partials beforehand, so the
+//           entries of blocks a small pass does not launch read as zero).
 // A run of RZ gates is one diagonal phase per amplitude: half tables over the tile's local
 // bits times a per-tile factor for the RZ gates on outer bits.
 #include <algorithm>
@@ -491,14 +493,18 @@ cudaError_t launch_fpass_inv(double2* v, const FPass& P, const FItem* items, con
 cudaError_t launch_gpass(const double2* psi, const double2* lam, const FPass& P,
                          const FItem* items, const DOp* gops, double* partial, cudaStream_t s) {
   (void)gops;
-  k_gpass<<<kRedBlocks, kFT, bpass_smem(P.m, P.n_slots), s>>>(psi, lam, P, items, partial);
+  const uint64_t ntiles = 1ull << __builtin_popcountll(P.outer_mask);
+  const int grid = (int)std::min<uint64_t>(ntiles, kRedBlocks);
+  k_gpass<<<grid, kFT, bpass_smem(P.m, P.n_slots), s>>>(psi, lam, P, items, partial);
   return cudaGetLastError();
 }
 
 cudaError_t launch_bpass(double2* psi, double2* lam, const FPass& P, const FItem* items,
                          const DOp* gops, const Rot* coef, const double* theta, double* partial,
                          cudaStream_t s) {
-  k_bpass<<<kRedBlocks, kFT, bpass_smem(P.m, P.n_slots), s>>>(psi, lam, P, items, gops, coef,
+  const uint64_t ntiles = 1ull << __builtin_popcountll(P.outer_mask);
+  const int grid = (int)std::min<uint64_t>(ntiles, kRedBlocks);
+  k_bpass<<<grid, kFT, bpass_smem(P.m, P.n_slots), s>>>(psi, lam, P, items, gops, coef,
                                                                theta, partial);
   return cudaGetLastError();
 }

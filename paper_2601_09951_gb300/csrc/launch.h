@@ -92,7 +92,8 @@ cudaError_t launch_dp_bwd_lam(const double2* lam, const double2* psi_b, double2*
 cudaError_t launch_gpass(const double2* psi, const double2* lam, const FPass& P,
                          const FItem* items, const DOp* gops, double* partial, cudaStream_t s);
 // Backward pass: partial[op * kRedBlocks + b] receives block b's gradient share of every
-// parameterised op of the pass.
+// parameterised op of the pass, for the min(tiles, kRedBlocks) blocks launched; the caller
+// zeroes the partials beforehand.
 cudaError_t launch_bpass(double2* psi, double2* lam, const FPass& P, const FItem* items,
                          const DOp* gops, const Rot* coef, const double* theta, double* partial,
                          cudaStream_t s);

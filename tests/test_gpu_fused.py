@@ -139,3 +139,51 @@ def test_checkpointed_layers_match_oracle_and_plain_sweep(make, budget_layers):
     ctx.set_checkpoint_bytes(0)
     e3, g3 = ctx.adjoint_grad(inst["circuit"], inst["theta"], H)
     assert e3 == e_plain and np.array_equal(g3, g_plain)
+
+
+def _dp_circuit(n, rng):
+    """Runs of RZ and CZ gates followed by CNOT and X runs (whole-state diagonal + permutation
+    segments), between single-qubit layers; wires span the low, middle and top bits."""
+    cb = W.CircuitBuilder(n)
+    for q in range(n):
+        cb.add(W.H, (q,))
+    for _ in range(3):
+        for q in rng.permutation(n)[: n // 2]:
+            cb.add(W.RY, (int(q),), param="new")
+        for q in rng.permutation(n)[:6]:
+            cb.add(W.RZ, (int(q),), param="new")
+        cb.add(W.CZ, (0, n - 1))
+        cb.add(W.CZ, (3, 7))
+        cb.add(W.RZ, (n - 1,), param="new")
+        for q in range(n - 1):
+            cb.add(W.CNOT, (q, q + 1))
+        cb.add(W.CNOT, (n - 1, 0))
+        cb.add(W.X, (5,))
+        cb.add(W.CNOT, (n - 2, 1))
+    return cb.build()
+
+
+@pytest.mark.parametrize("n,budget", [(14, 0), (15, 2), (16, 0)])
+def test_diagonal_permutation_segments(n, budget):
+    rng = np.random.default_rng(40 + n)
+    circ = _dp_circuit(n, rng)
+    theta = rng.uniform(-np.pi, np.pi, circ["n_params"])
+    inst = {"circuit": circ, "ham": W.random_pauli_sum(rng, n, 60, 0.5, 4, 1.0), "ref": 6,
+            "theta": theta, "name": f"dp_n{n}"}
+    ctx = svqe.Context(n)
+    ctx.set_checkpoint_bytes(budget * svqe.state_bytes(n))
+    # forward alone: the state, in the context's psi buffer
+    ctx.init_reference(inst["ref"])
+    ctx.apply_circuit(circ, theta)
+    want = oracle.state(circ, theta, inst["ref"])
+    assert np.max(np.abs(ctx.get_state() - want)) <= PSI_TOL
+    # energy and gradient
+    ctx.init_reference(inst["ref"])
+    H = svqe.Ham(ctx, inst["ham"])
+    e, g = ctx.adjoint_grad(circ, theta, H)
+    e0, g0 = oracle.energy_grad(inst)
+    assert_energy(e, e0, inst["ham"], inst["name"])
+    assert_grad(g, g0, inst["ham"], inst["name"])
+    ref = np.zeros(1 << n, np.complex128)
+    ref[inst["ref"]] = 1.0
+    assert np.max(np.abs(ctx.get_state() - ref)) <= 1e-12
