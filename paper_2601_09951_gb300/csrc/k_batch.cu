@@ -88,7 +88,7 @@ __device__ __forceinline__ Seg perm_part(const Seg& sg) {
 // conditional flips in order (inv = false: P) or in reverse order (inv = true: P^-1).  The
 // gates' masks are loaded in parallel (one lane per gate, at most kMaxPerm) and staged first.
 __device__ __forceinline__ void perm_setup(const Team& T, TeamS& S, const DOp* ops, const Seg& sg,
-                                           bool inv) {
+                                           bool inv, uint32_t N) {
   if (T.rank < sg.count) {
     const DOp& o = ops[sg.first + T.rank];
     const int l = inv ? sg.count - 1 - T.rank : T.rank;
@@ -99,12 +99,14 @@ __device__ __forceinline__ void perm_setup(const Team& T, TeamS& S, const DOp* o
   uint32_t c0 = 0;
   for (int l = 0; l < sg.count; ++l)
     if ((c0 & S.pm_lo[l]) == S.pm_lo[l]) c0 ^= S.pm_fl[l];
-  for (int j = T.rank; j < 128; j += T.size) {
-    uint32_t k = j < 64 ? (uint32_t)j : (uint32_t)(j - 64) << 6;
+  // only the entries an index below N can reach: min(64, N) low and max(1, N / 64) high
+  const int nlo = N < 64u ? (int)N : 64, nhi = N > 64u ? (int)(N >> 6) : 1;
+  for (int j = T.rank; j < nlo + nhi; j += T.size) {
+    uint32_t k = j < nlo ? (uint32_t)j : (uint32_t)(j - nlo) << 6;
     for (int l = 0; l < sg.count; ++l)
       if ((k & S.pm_lo[l]) == S.pm_lo[l]) k ^= S.pm_fl[l];
-    if (j < 64) S.pt_lo[j] = k;
-    else S.pt_hi[j - 64] = k ^ c0;
+    if (j < nlo) S.pt_lo[j] = k;
+    else S.pt_hi[j - nlo] = k ^ c0;
   }
   T.sync();
 }
@@ -454,6 +456,18 @@ __device__ __noinline__ void product_setup(const Team& T, TeamS& S, const DOp* o
   T.sync();
 }
 
+// b^t for t >= 1 by repeated squaring (about 2 log2 t multiplies instead of a transcendental
+// pow; the value depends on t alone, so one long call and many short calls agree bit for bit).
+__device__ __forceinline__ double ipow(double b, int t) {
+  double r = 1.0;
+  while (t > 0) {
+    if (t & 1) r *= b;
+    b *= b;
+    t >>= 1;
+  }
+  return r;
+}
+
 // Sign of the CZ gates of a diagonal segment at amplitude k (true = negative).
 __device__ __forceinline__ bool cz_sign(const TeamS& S, int ncz, uint32_t k) {
   uint32_t par = 0;
@@ -501,8 +515,10 @@ __device__ void run_instance(const BatchArgs& a, int idx, const Team& T, TeamS& 
     for (uint32_t k = tid; k < N; k += TS)
       psi[k] = make_double2(k == (uint32_t)I.ref ? 1.0 : 0.0, 0.0);
     // the group records and tables are first read by lambda = H psi, after the forward pass
-    team_prefetch_l2(T, groups, (int64_t)I.n_groups * (int64_t)sizeof(DGroup));
-    team_prefetch_l2(T, a.tables + I.tab_off, (int64_t)I.tab_n * (int64_t)sizeof(double2));
+    if (step == 0) {
+      team_prefetch_l2(T, groups, (int64_t)I.n_groups * (int64_t)sizeof(DGroup));
+      team_prefetch_l2(T, a.tables + I.tab_off, (int64_t)I.tab_n * (int64_t)sizeof(double2));
+    }
     T.sync();
 
     // ---------------------------------------------------------------- forward
@@ -516,7 +532,7 @@ __device__ void run_instance(const BatchArgs& a, int idx, const Team& T, TeamS& 
         // one pass: checkpoint psi[k], apply the phase, scatter to P k (the gates' conditional
         // flips in order)
         diag_setup(T, S, ops, coef, diag_part(sg), n);
-        perm_setup(T, S, ops, perm_part(sg), false);
+        perm_setup(T, S, ops, perm_part(sg), false, N);
         const int ncz = S.n_cz;
         double2* c = ck + (size_t)sg.ckpt * N;
         for (uint32_t k = tid; k < N; k += TS) {
@@ -533,7 +549,7 @@ __device__ void run_instance(const BatchArgs& a, int idx, const Team& T, TeamS& 
         lam = t;
       } else if (sg.kind == SEG_PERM) {
         // psi'[j] = psi[P^-1 j] with P = C_last ... C_first (each CNOT/X is its own inverse)
-        perm_setup(T, S, ops, sg, true);
+        perm_setup(T, S, ops, sg, true, N);
         for (uint32_t j = tid; j < N; j += TS) lam[j] = psi[perm_map(S, j)];
         T.sync();
         double2* t = psi;
@@ -690,7 +706,7 @@ __device__ void run_instance(const BatchArgs& a, int idx, const Team& T, TeamS& 
       if (sg.kind == SEG_PERM) {
         // lambda_before[j] = lambda_after[P j], gathered into the psi buffer (psi is reloaded
         // from the checkpoint below), then the buffers swap roles
-        perm_setup(T, S, ops, sg, false);
+        perm_setup(T, S, ops, sg, false, N);
         for (uint32_t j = tid; j < N; j += TS) psi[j] = lam[perm_map(S, j)];
         T.sync();
         double2* t = psi;
@@ -709,7 +725,7 @@ __device__ void run_instance(const BatchArgs& a, int idx, const Team& T, TeamS& 
         // un-phased lambda in registers until every gather of the team is done (at most kHU
         // amplitudes per thread in every team class)
         const int m = diag_setup(T, S, ops, coef, diag_part(sg), n);
-        perm_setup(T, S, ops, perm_part(sg), false);
+        perm_setup(T, S, ops, perm_part(sg), false, N);
         const int ncz = S.n_cz;
         constexpr int kHB = 4;
         constexpr int kHU = 16;
@@ -873,8 +889,8 @@ __device__ void run_instance(const BatchArgs& a, int idx, const Team& T, TeamS& 
           a.adam_m[q] = m;
           a.adam_v[q] = v;
           const int t = a.adam_t0 + step + 1;
-          const double mh = m / (1.0 - pow(a.beta1, (double)t));
-          const double vh = v / (1.0 - pow(a.beta2, (double)t));
+          const double mh = m / (1.0 - ipow(a.beta1, t));
+          const double vh = v / (1.0 - ipow(a.beta2, t));
           theta[p] -= lr * mh / (sqrt(vh) + a.eps);
         } else {
           theta[p] = fma(-lr, g, theta[p]);
