@@ -46,9 +46,12 @@ def parse():
     ap.add_argument("--requests", type=int, default=300)
     ap.add_argument("--qubits", type=int, default=28)
     ap.add_argument("--ansatz", default="hea", choices=["hea", "uccsd"])
-    ap.add_argument("--checkpoint-gb", type=float, default=64.0,
+    ap.add_argument("--checkpoint-gb", type=float, default=0.0,
                     help="single: device memory for psi checkpoints of commuting layers "
-                         "(sv_set_checkpoint_bytes); 0 keeps psi and lambda only")
+                         "(sv_set_checkpoint_bytes); the default 0 keeps at most three "
+                         "state-sized buffers")
+    ap.add_argument("--per-circuit-sample", type=int, default=512,
+                    help="batch: instances timed through the one-circuit-per-launch path")
     return ap.parse_args()
 
 
@@ -379,6 +382,46 @@ def run_single(args):
                       "dtype": "f64"}), flush=True)
 
 
+def per_circuit(insts, sample):
+    """The plain one-circuit-per-launch path on the same instances: each instance's energy and
+    adjoint gradient through a single-state context (sv_adjoint_grad_dev: per-gate kernels),
+    one after another on one stream, for the first `sample` instances.  evals/s from CUDA
+    events; launches per evaluation counted from the op lists."""
+    import torch
+    from paper_2601_09951_gb300 import svqe
+    stream = torch.cuda.Stream()
+    ctxs, prepared, launches = {}, [], 0
+    for inst in insts[:sample]:
+        n = inst["circuit"]["n"]
+        if n not in ctxs:
+            ctxs[n] = svqe.Context(n, stream=stream.cuda_stream)
+            ctxs[n].init_reference(inst["ref"])
+        C = svqe.Circuit(inst["circuit"])
+        H = svqe.Ham(ctxs[n], inst["ham"])
+        th = torch.tensor(np.asarray(inst["theta"], dtype=np.float64), device="cuda")
+        g = torch.zeros(max(C.n_params, 1), dtype=torch.float64, device="cuda")
+        prepared.append((ctxs[n], C, th, H, g))
+        # init, coefficients, one forward and one adjoint kernel per gate, H psi + sum,
+        # per-op contributions + per-parameter sums
+        launches += 2 * len(C.gates) + 6
+    e = torch.zeros(1, dtype=torch.float64, device="cuda")
+    for ctx, C, th, H, g in prepared:
+        ctx.adjoint_grad_dev(C, th.data_ptr(), H, e.data_ptr(), g.data_ptr())
+    torch.cuda.synchronize()
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    t0.record(stream)
+    for ctx, C, th, H, g in prepared:
+        ctx.adjoint_grad_dev(C, th.data_ptr(), H, e.data_ptr(), g.data_ptr())
+    t1.record(stream)
+    torch.cuda.synchronize()
+    s = t0.elapsed_time(t1) / 1e3
+    return {"value": len(prepared) / s, "unit": "evals/s",
+            "sample": f"instances 0..{len(prepared) - 1} of the same workload, one "
+                      "sv_adjoint_grad_dev per instance in sequence on one stream",
+            "launches_per_eval": launches / len(prepared)}
+
+
 def run_classes(args):
     """Batched-kernel throughput by register size: for each n, a batch of instances of that n
     alone (hardware-efficient ansatz, 5 layers, 275 terms), enough to give every CTA several
@@ -454,6 +497,34 @@ def run_h2(args):
             if rep >= max(3, args.warmup):
                 times.append(t0.elapsed_time(t1) / 1e3)
     gpu_s = float(np.median(times))
+    # configuration 1 of the batched workloads: 100 bond lengths x 50 gradient-descent steps
+    # at eta = 0.4 from theta = 0 (5000 evaluations): one persistent launch, against the
+    # one-circuit path (vqe_step per bond length on one context)
+    gd = []
+    with torch.cuda.stream(stream):
+        for rep in range(max(3, args.warmup) + max(1, args.steps)):
+            th.zero_()
+            t0 = torch.cuda.Event(enable_timing=True)
+            t1 = torch.cuda.Event(enable_timing=True)
+            t0.record(stream)
+            b.vqe_dev(th.data_ptr(), 0.4, 50, None)
+            t1.record(stream)
+            torch.cuda.synchronize()
+            if rep >= max(3, args.warmup):
+                gd.append(t0.elapsed_time(t1) / 1e3)
+    gd_s = float(np.median(gd))
+    ctx = svqe.Context(4, stream=stream.cuda_stream)
+    prepared = [(svqe.Circuit(i["circuit"]), svqe.Ham(ctx, i["ham"]), i["ref"]) for i in insts]
+    for C, H, ref in prepared[:5]:
+        ctx.init_reference(ref)
+        ctx.vqe_step(C, H, np.zeros(C.n_params), 0.4, 50)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for C, H, ref in prepared:
+        ctx.init_reference(ref)
+        ctx.vqe_step(C, H, np.zeros(C.n_params), 0.4, 50)
+    torch.cuda.synchronize()
+    serial_gd_s = time.perf_counter() - t0
     oracle.set_threads(1)
     t0 = time.perf_counter()
     sample = [0, 50, 99]
@@ -468,6 +539,11 @@ def run_h2(args):
         "oracle_sample": f"bonds {sample}, 300 Adam steps each, 1 thread",
         "paper_context_s": {"serial PennyLane Adam, 1 CPU core": 593.95,
                             "lightning.gpu, 1 H100": 164.91, "MPI-32 Optax+JIT": 5.04},
+        "gd50": {"what": "100 bond lengths x 50 gradient-descent steps, eta = 0.4, theta0 = 0",
+                 "batched_s": gd_s, "batched_evals_per_s": 5000 / gd_s,
+                 "per_circuit_s": serial_gd_s, "per_circuit_evals_per_s": 5000 / serial_gd_s,
+                 "per_circuit_path": "vqe_step per bond length on one 4-qubit context "
+                                     "(host wall time, energies copied back per call)"},
         "data": "synthetic coefficients with the H2 Jordan-Wigner structure"}), flush=True)
 
 
@@ -585,6 +661,10 @@ def main():
         "clocks": clocks,
         "wall_s_incl_l2_flush": wall,
     }
+    if world == 1 and args.per_circuit_sample > 0:
+        pc = per_circuit(insts, args.per_circuit_sample)
+        pc["batched_over_per_circuit"] = value / pc["value"]
+        line["per_circuit"] = pc
     if world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(args, args.cpu_seconds)
     print(json.dumps(line), flush=True)
