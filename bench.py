@@ -50,6 +50,8 @@ def parse():
                     help="single: device memory for psi checkpoints of commuting layers "
                          "(sv_set_checkpoint_bytes); the default 0 keeps at most three "
                          "state-sized buffers")
+    ap.add_argument("--autotune", action="store_true",
+                    help="single: autotune the fused tile size first (sv_set_autotune)")
     ap.add_argument("--per-circuit-sample", type=int, default=512,
                     help="batch: instances timed through the one-circuit-per-launch path")
     return ap.parse_args()
@@ -355,6 +357,8 @@ def run_single(args):
     stream = torch.cuda.Stream()
     ctx = svqe.Context(n, stream=stream.cuda_stream)
     ctx.set_checkpoint_bytes(int(args.checkpoint_gb * 2**30))
+    if args.autotune:
+        ctx.set_autotune(True)
     ctx.init_reference(inst["ref"])
     H = svqe.Ham(ctx, inst["ham"])
     C = svqe.Circuit(inst["circuit"])
@@ -378,6 +382,7 @@ def run_single(args):
                       "workload": inst["name"], "n_qubits": n, "gates": len(C.gates),
                       "terms": len(inst["ham"]["coeff"]), "groups": H.info()[0],
                       "checkpoint_bytes": int(args.checkpoint_gb * 2**30),
+                      "tile_bits": ctx.tile_bits(), "autotuned": bool(args.autotune),
                       "ms_per_eval": ms, "value": 1e3 / ms, "unit": "evals/s",
                       "dtype": "f64"}), flush=True)
 

@@ -136,6 +136,17 @@ sv_status sv_destroy(sv_ctx* ctx);
  * the device allows.  A smaller budget frees the buffers beyond it; SV_EINVAL for a NULL
  * handle. */
 sv_status sv_set_checkpoint_bytes(sv_ctx* ctx, uint64_t bytes);
+/* Autotuning of the fused-pass tile size (registers of at least 14 qubits); off by default
+ * (tiles of 2^11 amplitudes).  When on, the first sv_adjoint_grad* / vqe_step call with a
+ * circuit structure not seen before in the process does the following.  Gate types and wires
+ * count as structure; angles do not.  It times the forward pass with tiles of 2^9, 2^10 and
+ * 2^11 amplitudes and keeps the fastest.  That call therefore runs three extra forward passes
+ * on psi, which the evaluation re-initialises.  Results are shared by every context of the
+ * process.  If the environment variable SVQE_TUNE_CACHE names a file, results are read from
+ * and appended to it as "n key bits" lines.  SV_EINVAL for a NULL handle. */
+sv_status sv_set_autotune(sv_ctx* ctx, int32_t enable);
+/* Tile size (bits) of the fused passes of the last circuit staged on the context. */
+sv_status sv_tile_bits(const sv_ctx* ctx, int32_t* tile_bits);
 
 /* ---------------------------------------------------------------- Hamiltonians */
 

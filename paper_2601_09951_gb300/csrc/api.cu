@@ -4,9 +4,12 @@
 
 #include <algorithm>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <numeric>
+#include <unordered_map>
 #include <vector>
 
 #include "../../include/svqe.h"
@@ -65,6 +68,8 @@ struct sv_ctx {
     DpArgs dp;         // CH_DP
   };
   std::vector<Chunk> chunks;
+  int tune = 0;         // sv_set_autotune
+  int tile_bits = 11;   // tile size of the staged circuit's fused passes
 };
 
 struct sv_ham {
@@ -369,7 +374,10 @@ sv_status sv_init_reference(sv_ctx* c, uint64_t b) {
 }
 
 // Upload a lowered circuit's ops and make sure every circuit-sized buffer fits.
-sv_status svqe::stage_circuit(sv_ctx* c, const HostCircuit& hc) {
+static sv_status plan_circuit(sv_ctx* c, const HostCircuit& hc, int tile_bits);
+static int tune_tile_bits(sv_ctx* c, const HostCircuit& hc);
+
+sv_status svqe::stage_circuit(sv_ctx* c, const HostCircuit& hc, bool may_tune) {
   const size_t n_ops = hc.ops.size();
   SV_CUDA(grow(c->ops, c->ops_cap, n_ops), c);
   SV_CUDA(grow(c->coef, c->coef_cap, n_ops), c);
@@ -380,6 +388,16 @@ sv_status svqe::stage_circuit(sv_ctx* c, const HostCircuit& hc) {
   if (n_ops)
     SV_CUDA(cudaMemcpyAsync(c->ops, hc.ops.data(), n_ops * sizeof(DOp), cudaMemcpyHostToDevice,
                             c->stream), c);
+  int m = fused_tile_bits();
+  if (may_tune && c->tune && c->n >= kFusedMinQubits && n_ops > 0) m = tune_tile_bits(c, hc);
+  if (m <= 0) return SV_ECUDA;
+  return plan_circuit(c, hc, m);
+}
+
+// Fused-pass plan of a staged circuit with tiles of tile_bits bits (see stage_circuit).
+static sv_status plan_circuit(sv_ctx* c, const HostCircuit& hc, int tile_bits) {
+  const size_t n_ops = hc.ops.size();
+  c->tile_bits = tile_bits;
   c->plan.passes.clear();
   c->plan.items.clear();
   c->chunks.clear();
@@ -432,7 +450,7 @@ sv_status svqe::stage_circuit(sv_ctx* c, const HostCircuit& hc) {
     auto plan_chunk = [&](int kind, int first, int count, int ckid) {
       const std::vector<DOp> sub(hc.ops.begin() + first, hc.ops.begin() + first + count);
       HostPlan sp;
-      plan_passes(sub, c->n, fused_tile_bits(), sp);
+      plan_passes(sub, c->n, tile_bits, sp);
       sv_ctx::Chunk ch{};
       ch.kind = kind;
       ch.first = first;
@@ -579,6 +597,111 @@ static sv_status forward(sv_ctx* c, const HostCircuit& hc, const double* theta_d
   return SV_OK;
 }
 
+// ------------------------------------------------------------------------------ autotuner
+// The fused tile size (2^9 .. 2^11 amplitudes per tile) trades shared memory per block, and so
+// occupancy, against the number of passes a circuit needs.  The tuner keys a process-wide
+// cache by the circuit's structure (gate types and wires, not the angles).  The cache is
+// optionally kept in the text file named by SVQE_TUNE_CACHE, one "n key bits" line per
+// entry.  A miss times the forward pass with each tile size (CUDA events, the second of two
+// runs) and keeps the fastest.
+static std::mutex g_tune_mu;
+static std::unordered_map<uint64_t, int> g_tune;
+static bool g_tune_loaded = false;
+
+static uint64_t structure_key(int n, const HostCircuit& hc) {
+  uint64_t h = 1469598103934665603ull ^ (uint64_t)n;
+  auto mix = [&h](uint64_t v) {
+    h ^= v;
+    h *= 1099511628211ull;
+  };
+  for (const DOp& op : hc.ops) {
+    mix((uint64_t)op.type);
+    mix(op.lo_or);
+    mix(op.flip);
+    mix((uint64_t)op.k | (uint64_t)op.sb[0] << 8 | (uint64_t)op.sb[1] << 16 |
+        (uint64_t)op.sb[2] << 24 | (uint64_t)op.sb[3] << 32);
+  }
+  return h;
+}
+
+static int tune_tile_bits(sv_ctx* c, const HostCircuit& hc) {
+  const uint64_t key = structure_key(c->n, hc);
+  const char* path = std::getenv("SVQE_TUNE_CACHE");
+  {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    if (!g_tune_loaded) {
+      g_tune_loaded = true;
+      if (path) {
+        if (FILE* f = std::fopen(path, "r")) {
+          int n = 0, bits = 0;
+          unsigned long long k = 0;
+          while (std::fscanf(f, "%d %llu %d", &n, &k, &bits) == 3)
+            if (bits >= 9 && bits <= 11) g_tune[(uint64_t)k] = bits;
+          std::fclose(f);
+        }
+      }
+    }
+    const auto it = g_tune.find(key);
+    if (it != g_tune.end()) return it->second;
+  }
+  // the angles do not change the passes: time with theta = 0
+  if (hc.n_params > 0 &&
+      cudaMemsetAsync(c->theta, 0, (size_t)hc.n_params * sizeof(double), c->stream) != cudaSuccess)
+    return -1;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+    cudaGetLastError();
+    if (e0) cudaEventDestroy(e0);
+    return -1;
+  }
+  int best = fused_tile_bits();
+  float best_ms = 1e30f;
+  bool ok = true;
+  for (int m = 9; m <= 11 && ok; ++m) {
+    ok = plan_circuit(c, hc, m) == SV_OK;
+    float ms = 0.0f;
+    for (int rep = 0; rep < 2 && ok; ++rep) {
+      double2* out = nullptr;
+      ok = launch_init_basis(c->psi, c->n, c->ref, c->stream) == cudaSuccess &&
+           cudaEventRecord(e0, c->stream) == cudaSuccess &&
+           forward(c, hc, c->theta, false, &out) == SV_OK &&
+           cudaEventRecord(e1, c->stream) == cudaSuccess &&
+           cudaEventSynchronize(e1) == cudaSuccess &&
+           cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess;
+    }
+    if (ok && ms < best_ms) {
+      best_ms = ms;
+      best = m;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (!ok) return -1;
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  g_tune[key] = best;
+  if (path) {
+    if (FILE* f = std::fopen(path, "a")) {
+      std::fprintf(f, "%d %llu %d\n", c->n, (unsigned long long)key, best);
+      std::fclose(f);
+    }
+  }
+  return best;
+}
+
+sv_status sv_set_autotune(sv_ctx* c, int32_t enable) {
+  clear_error();
+  if (!c) { set_error("NULL handle"); return SV_EINVAL; }
+  c->tune = enable ? 1 : 0;
+  return SV_OK;
+}
+
+sv_status sv_tile_bits(const sv_ctx* c, int32_t* tile_bits) {
+  clear_error();
+  if (!c || !tile_bits) { set_error("NULL argument"); return SV_EINVAL; }
+  *tile_bits = c->tile_bits;
+  return SV_OK;
+}
+
 // psi = |ref>, forward, lambda = H psi, adjoint sweep; energy -> energy_dev[0], gradient ->
 // grad_dev.  Everything stream-ordered on c->stream.
 sv_status svqe::adjoint_core(sv_ctx* c, const HostCircuit& hc, const sv_ham* H,
@@ -700,7 +823,7 @@ sv_status sv_adjoint_grad_dev(sv_ctx* c, const sv_circuit* circ, const double* t
   sv_status st = lower_circuit(circ, c->n, hc);
   if (st != SV_OK) return st;
   if (hc.n_params > 0 && (!theta_dev || !grad_dev)) { set_error("theta/grad is NULL"); return SV_EINVAL; }
-  if ((st = stage_circuit(c, hc)) != SV_OK) return st;
+  if ((st = stage_circuit(c, hc, true)) != SV_OK) return st;
   return adjoint_core(c, hc, H, theta_dev, energy_dev, grad_dev);
 }
 
@@ -714,7 +837,7 @@ sv_status sv_adjoint_grad(sv_ctx* c, const sv_circuit* circ, const double* theta
   sv_status st = lower_circuit(circ, c->n, hc);
   if (st != SV_OK) return st;
   if (hc.n_params > 0 && (!theta || !grad_out)) { set_error("theta/grad is NULL"); return SV_EINVAL; }
-  if ((st = stage_circuit(c, hc)) != SV_OK) return st;
+  if ((st = stage_circuit(c, hc, true)) != SV_OK) return st;
   if (hc.n_params)
     SV_CUDA(cudaMemcpyAsync(c->theta, theta, hc.n_params * sizeof(double),
                             cudaMemcpyHostToDevice, c->stream), c);
@@ -730,7 +853,7 @@ sv_status sv_adjoint_grad(sv_ctx* c, const sv_circuit* circ, const double* theta
 
 sv_status svqe::vqe_enqueue(sv_ctx* c, const HostCircuit& hc, const sv_ham* H, const double* theta_in,
                       double lr, int32_t n_steps, double* theta_out, double* energy_out) {
-  sv_status st = stage_circuit(c, hc);
+  sv_status st = stage_circuit(c, hc, true);
   if (st != SV_OK) return st;
   SV_CUDA(grow(c->etraj, c->etraj_cap, (size_t)std::max(1, n_steps)), c);
   if (hc.n_params)

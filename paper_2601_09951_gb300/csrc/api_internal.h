@@ -12,7 +12,11 @@
 namespace svqe {
 
 // Stage a lowered circuit on a context (ops, coefficient and gradient buffers, fused plan).
-sv_status stage_circuit(sv_ctx* c, const HostCircuit& hc);
+// Upload a lowered circuit and plan its fused passes.  may_tune: with autotuning on
+// (sv_set_autotune), a circuit structure not seen before has its tile size measured first
+// (the forward pass is run on the context's psi, so only callers that re-initialise psi
+// afterwards pass true).
+sv_status stage_circuit(sv_ctx* c, const HostCircuit& hc, bool may_tune = false);
 // psi = |ref>, forward, lambda = H psi, adjoint sweep; stream-ordered.
 sv_status adjoint_core(sv_ctx* c, const HostCircuit& hc, const sv_ham* H,
                        const double* theta_dev, double* energy_dev, double* grad_dev);

@@ -73,6 +73,8 @@ def lib():
         "sv_create": ([P, i32, P], i32),
         "sv_destroy": ([P], i32),
         "sv_set_checkpoint_bytes": ([P, u64], i32),
+        "sv_set_autotune": ([P, i32], i32),
+        "sv_tile_bits": ([P, P], i32),
         "sv_ham_upload": ([P, P, P], i32),
         "sv_ham_free": ([P], i32),
         "sv_ham_info": ([P, P, P], i32),
@@ -312,6 +314,16 @@ class Context:
     def set_checkpoint_bytes(self, nbytes):
         """Device memory for psi checkpoints of commuting layers (sv_set_checkpoint_bytes)."""
         _check(lib().sv_set_checkpoint_bytes(self._c, int(nbytes)))
+
+    def set_autotune(self, enable=True):
+        """Autotune the fused-pass tile size per circuit structure (sv_set_autotune)."""
+        _check(lib().sv_set_autotune(self._c, 1 if enable else 0))
+
+    def tile_bits(self):
+        """Tile size (bits) of the last staged circuit's fused passes."""
+        t = ctypes.c_int32()
+        _check(lib().sv_tile_bits(self._c, ctypes.byref(t)))
+        return t.value
 
     def set_state(self, psi):
         a = np.ascontiguousarray(psi, dtype=np.complex128)

@@ -187,3 +187,39 @@ def test_diagonal_permutation_segments(n, budget):
     ref = np.zeros(1 << n, np.complex128)
     ref[inst["ref"]] = 1.0
     assert np.max(np.abs(ctx.get_state() - ref)) <= 1e-12
+
+
+def test_tile_size_autotuner(tmp_path, monkeypatch):
+    """With autotuning on, the first evaluation of a circuit structure times tiles of 2^9..2^11
+    amplitudes and keeps the fastest; the choice is cached for every context of the process
+    (and appended to SVQE_TUNE_CACHE), and the result matches the oracle and the default
+    tile size."""
+    cache = tmp_path / "tune.txt"
+    monkeypatch.setenv("SVQE_TUNE_CACHE", str(cache))
+    inst = W.uccsd_instance(n=15, n_elec=8, n_singles=12, n_doubles=20, n_terms=200, seed=44)
+    n = inst["circuit"]["n"]
+    plain = svqe.Context(n)
+    plain.init_reference(inst["ref"])
+    Hp = svqe.Ham(plain, inst["ham"])
+    e_plain, g_plain = plain.adjoint_grad(inst["circuit"], inst["theta"], Hp)
+    assert plain.tile_bits() == 11
+    ctx = svqe.Context(n)
+    ctx.set_autotune(True)
+    ctx.init_reference(inst["ref"])
+    H = svqe.Ham(ctx, inst["ham"])
+    e, g = ctx.adjoint_grad(inst["circuit"], inst["theta"], H)
+    bits = ctx.tile_bits()
+    assert bits in (9, 10, 11)
+    e0, g0 = oracle.energy_grad(inst)
+    assert_energy(e, e0, inst["ham"], inst["name"])
+    assert_grad(g, g0, inst["ham"], inst["name"])
+    assert abs(e - e_plain) <= 1e-12 * max(1.0, abs(e_plain))
+    np.testing.assert_allclose(g, g_plain, rtol=0, atol=1e-10 * max(1.0, np.abs(g_plain).max()))
+    other = svqe.Context(n)
+    other.set_autotune(True)
+    other.init_reference(inst["ref"])
+    H2 = svqe.Ham(other, inst["ham"])
+    e2, g2 = other.adjoint_grad(inst["circuit"], inst["theta"], H2)
+    assert other.tile_bits() == bits and e2 == e and np.array_equal(g2, g)
+    lines = cache.read_text().split("\n")
+    assert any(line.startswith(f"{n} ") and line.endswith(f" {bits}") for line in lines)
