@@ -556,6 +556,16 @@ static sv_status plan_circuit(sv_ctx* c, const HostCircuit& hc, int tile_bits) {
   return SV_OK;
 }
 
+// A pass that holds a single gate runs as that gate's own kernel (k_apply / k_adjoint): it
+// touches only the gate's amplitudes (half the state for a CNOT, an eighth for a
+// DoubleExcitation) instead of staging every tile.  Returns the op, or -1.
+static int single_op(const sv_ctx* c, int p) {
+  const FPass& P = c->plan.passes[p];
+  if (P.n_items != 1) return -1;
+  const FItem& it = c->plan.items[P.first_item];
+  return it.kind == 0 ? it.op : -1;
+}
+
 // The state buffers a whole-state segment may write: psi, lambda and the scratch buffer.
 static double2* free_buffer(sv_ctx* c, const double2* a, const double2* b) {
   double2* pool[3] = {c->lam, c->scratch, c->psi};
@@ -585,9 +595,14 @@ static sv_status forward(sv_ctx* c, const HostCircuit& hc, const double* theta_d
       if (save && ch.kind == sv_ctx::CH_LAYER)
         SV_CUDA(cudaMemcpyAsync(c->ck[ch.ck], psi, sv_state_bytes(c->n),
                                 cudaMemcpyDeviceToDevice, c->stream), c);
-      for (int p = ch.p0; p < ch.p1; ++p)
-        SV_CUDA(launch_fpass(psi, c->plan.passes[p], c->items, c->ops, c->coef, theta_dev,
-                             c->stream), c);
+      for (int p = ch.p0; p < ch.p1; ++p) {
+        const int op = single_op(c, p);
+        if (op >= 0)
+          SV_CUDA(launch_apply_op(psi, c->n, hc.ops[op], c->coef + op, false, c->stream), c);
+        else
+          SV_CUDA(launch_fpass(psi, c->plan.passes[p], c->items, c->ops, c->coef, theta_dev,
+                               c->stream), c);
+      }
     }
     *psi_out = psi;
     return SV_OK;
@@ -722,9 +737,17 @@ sv_status svqe::adjoint_core(sv_ctx* c, const HostCircuit& hc, const sv_ham* H,
     for (int ci = (int)c->chunks.size() - 1; ci >= 0; --ci) {
       const sv_ctx::Chunk& ch = c->chunks[ci];
       if (ch.kind == sv_ctx::CH_PASSES) {
-        for (int p = ch.p1 - 1; p >= ch.p0; --p)
-          SV_CUDA(launch_bpass(psi, lam, c->plan.passes[p], c->items, c->ops, c->coef,
-                               theta_dev, c->gpart, c->stream), c);
+        for (int p = ch.p1 - 1; p >= ch.p0; --p) {
+          const int op = single_op(c, p);
+          if (op >= 0) {
+            double* part = hc.ops[op].param >= 0 ? c->gpart + (size_t)op * kRedBlocks : nullptr;
+            SV_CUDA(launch_adjoint_op(psi, lam, c->n, hc.ops[op], c->coef + op, part,
+                                      c->stream), c);
+          } else {
+            SV_CUDA(launch_bpass(psi, lam, c->plan.passes[p], c->items, c->ops, c->coef,
+                                 theta_dev, c->gpart, c->stream), c);
+          }
+        }
       } else if (ch.kind == sv_ctx::CH_LAYER) {
         // a checkpointed commuting layer: every gradient from (psi, lambda) at the layer's
         // end, then the layer un-applied to lambda alone; psi before the layer is the
