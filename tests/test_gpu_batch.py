@@ -134,3 +134,32 @@ def test_on_device_adam_h2_sweep_paper_settings():
         b.adam_dev(th1.data_ptr(), 0.01, 1, None, reset=False)
     torch.cuda.synchronize()
     assert np.array_equal(th1.cpu().numpy(), th.cpu().numpy())
+
+
+def test_product_layer_from_any_reference_and_partial_layers():
+    """A first RY layer on the reference basis state is written directly as a product state.
+    Cover references other than |0...0>, first layers that leave qubits out, an RX first layer
+    (not a product layer) and one-qubit layers, against the oracle."""
+    rng = np.random.default_rng(71)
+    insts = []
+    for n in (1, 2, 3, 5, 8, 10, 11, 12):
+        for variant in range(3):
+            cb = W.CircuitBuilder(n)
+            qs = list(range(n)) if variant == 0 else [int(q) for q in rng.permutation(n)[: max(1, n - 2)]]
+            first = W.RX if variant == 2 else W.RY
+            for q in qs:
+                cb.add(first, (q,), param="new")
+            for q in range(n):
+                cb.add(W.RZ, (q,), param="new")
+            for q in range(n - 1):
+                cb.add(W.CNOT, (q, q + 1))
+            for q in range(n):
+                cb.add(W.RY, (q,), param="new")
+            circ = cb.build()
+            insts.append({"circuit": circ, "ham": W.random_pauli_sum(rng, n, 30, 0.6, 3, 1.0),
+                          "ref": int(rng.integers(0, 1 << n)),
+                          "theta": rng.uniform(-np.pi, np.pi, circ["n_params"]),
+                          "name": f"product_n{n}_v{variant}"})
+    b = svqe.Batch(insts)
+    e, g = b.run(b.theta_of(insts))
+    _check(b, insts, e, g)
