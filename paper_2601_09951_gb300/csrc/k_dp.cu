@@ -28,7 +28,6 @@ namespace {
 constexpr int kDT = 256;     // threads per CTA
 constexpr int kDB = 11;      // bits per block
 constexpr int kDBlock = 1 << kDB;
-constexpr int kMaxHigh = 20; // block-index bits (n <= 31)
 
 __device__ __forceinline__ double2 cmul(const double2& a, const double2& b) {
   return make_double2(fma(a.x, b.x, dneg(a.y) * b.y), fma(a.x, b.y, a.y * b.x));
@@ -106,8 +105,11 @@ __global__ void __launch_bounds__(kDT) k_dp_bwd_psi(const double2* __restrict__ 
 
 // Backward, lambda: out[k] = conj(phase(k)) lam[P(k)], and the RZ gradient shares from
 // w_k = Im(conj(out[k]) psi_b[k]) with psi_b the un-phased psi (k_dp_bwd_psi's output):
-// partial[op * kRedBlocks + block] for every parameterised RZ op of the segment.
-__global__ void __launch_bounds__(kDT) k_dp_bwd_lam(const double2* __restrict__ lam,
+// partial[op * kRedBlocks + block] for every parameterised RZ op of the segment.  The first
+// G = min(blocks, 1024) CTAs do the work, CTA c taking blocks c, c + G, c + 2G, ...: block-index
+// bits below log2 G are fixed per CTA (their signs apply to the CTA's total), and the bits
+// above it are bits of the round r (one sum each, at most 10).  The other CTAs write zeros.
+__global__ void __launch_bounds__(kDT, 2) k_dp_bwd_lam(const double2* __restrict__ lam,
                                                     const double2* __restrict__ psi_b,
                                                     double2* __restrict__ out, DpArgs a,
                                                     double* __restrict__ partial) {
@@ -115,30 +117,36 @@ __global__ void __launch_bounds__(kDT) k_dp_bwd_lam(const double2* __restrict__ 
   DpShared& S = *reinterpret_cast<DpShared*>(dsm);
   dp_stage(S, a);
   const uint64_t nblk = a.N >> kDB;
-  const int nhigh = a.n - kDB;
-  double W = 0.0, mid[3] = {0.0, 0.0, 0.0}, high[kMaxHigh];
+  const uint64_t G = nblk < 1024 ? nblk : 1024;
+  const int lg = __popcll(G - 1);  // log2 G
+  const int nrb = a.n - kDB - lg;  // round bits
+  constexpr int kMaxRound = 10;
+  double W = 0.0, mid[3] = {0.0, 0.0, 0.0}, hr[kMaxRound];
 #pragma unroll
-  for (int b = 0; b < kMaxHigh; ++b) high[b] = 0.0;
-  for (uint64_t blk = blockIdx.x; blk < nblk; blk += gridDim.x) {
-    const double2 o = dp_outer(a, blk);
-    double wb = 0.0;
+  for (int b = 0; b < kMaxRound; ++b) hr[b] = 0.0;
+  if (blockIdx.x < G) {
+    uint64_t r = 0;
+    for (uint64_t blk = blockIdx.x; blk < nblk; blk += G, ++r) {
+      const double2 o = dp_outer(a, blk);
+      double wb = 0.0;
 #pragma unroll
-    for (int i = 0; i < kDBlock / kDT; ++i) {
-      const uint32_t j = threadIdx.x + i * kDT;
-      const uint64_t k = (blk << kDB) | j;
-      double2 v = cmul_conj(lam[dp_map(S, k)], cmul(S.p0[j], o));
-      if (a.n_cz && dp_cz(a, k)) v = make_double2(dneg(v.x), dneg(v.y));
-      out[k] = v;
-      const double2 p = psi_b[k];
-      const double w = fma(v.x, p.y, dneg(v.y) * p.x);
-      wb += w;
+      for (int i = 0; i < kDBlock / kDT; ++i) {
+        const uint32_t j = threadIdx.x + i * kDT;
+        const uint64_t k = (blk << kDB) | j;
+        double2 v = cmul_conj(lam[dp_map(S, k)], cmul(S.p0[j], o));
+        if (a.n_cz && dp_cz(a, k)) v = make_double2(dneg(v.x), dneg(v.y));
+        out[k] = v;
+        const double2 p = psi_b[k];
+        const double w = fma(v.x, p.y, dneg(v.y) * p.x);
+        wb += w;
 #pragma unroll
-      for (int q = 0; q < 3; ++q) mid[q] += ((i >> q) & 1) ? dneg(w) : w;
+        for (int q = 0; q < 3; ++q) mid[q] += ((i >> q) & 1) ? dneg(w) : w;
+      }
+      W += wb;
+#pragma unroll
+      for (int b = 0; b < kMaxRound; ++b)
+        if (b < nrb) hr[b] += ((r >> b) & 1ull) ? dneg(wb) : wb;
     }
-    W += wb;
-#pragma unroll
-    for (int b = 0; b < kMaxHigh; ++b)
-      if (b < nhigh) high[b] += ((blk >> b) & 1ull) ? dneg(wb) : wb;
   }
   // one CTA reduction per parameterised RZ op
   const int tid = threadIdx.x;
@@ -149,11 +157,13 @@ __global__ void __launch_bounds__(kDT) k_dp_bwd_lam(const double2* __restrict__ 
       v = ((tid >> bit) & 1) ? dneg(W) : W;
     } else if (bit < kDB) {
       v = bit == 8 ? mid[0] : bit == 9 ? mid[1] : mid[2];
+    } else if (bit < kDB + lg) {
+      v = ((blockIdx.x >> (bit - kDB)) & 1u) ? dneg(W) : W;
     } else {
       v = 0.0;
 #pragma unroll
-      for (int b = 0; b < kMaxHigh; ++b)
-        if (b == bit - kDB) v = high[b];
+      for (int b = 0; b < kMaxRound; ++b)
+        if (b == bit - kDB - lg) v = hr[b];
     }
     v = warp_sum(v);
     if ((tid & 31) == 0) S.red[tid >> 5] = v;
