@@ -252,6 +252,7 @@ struct Unit {      // a schedulable unit: one op, or a run of RZ ops (diagonal i
 }  // namespace
 
 void plan_passes(const std::vector<DOp>& ops, int n, int m, HostPlan& plan) {
+  const int min_low = n <= kL2Qubits ? kMinLowBitsL2 : kMinLowBits;
   plan.passes.clear();
   plan.items.clear();
   std::vector<Unit> units;
@@ -278,7 +279,7 @@ void plan_passes(const std::vector<DOp>& ops, int n, int m, HostPlan& plan) {
     ++l;
   }
   m = std::min(m, n);
-  const uint64_t low = (1ull << std::min(kMinLowBits, n)) - 1ull;
+  const uint64_t low = (1ull << std::min(min_low, n)) - 1ull;
   std::vector<char> done(units.size(), 0);
   size_t left = units.size();
   while (left > 0) {

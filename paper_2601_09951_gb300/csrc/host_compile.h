@@ -55,6 +55,7 @@ std::vector<std::pair<int, int>> commuting_layers(const std::vector<DOp>& ops, i
 // move ahead of ops skipped for this pass only if it shares no qubit with them (so it
 // commutes with them).  Runs of >= 3 consecutive RZ gates become one diagonal item (at most
 // one per pass, at most kMaxSlots RZ gates).  A pass holds at most kMaxSlots gradient slots.
+// Every tile includes the kMinLowBits lowest bits (kMinLowBitsL2 for n <= kL2Qubits).
 constexpr int kMaxSlots = kMaxSlotsDev;
 struct HostPlan {
   std::vector<FPass> passes;

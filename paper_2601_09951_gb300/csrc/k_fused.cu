@@ -240,7 +240,7 @@ __global__ void __launch_bounds__(kFT) k_fpass(double2* __restrict__ psi, FPass 
                                                const Rot* __restrict__ coef,
                                                const double* __restrict__ theta) {
   extern __shared__ double2 tile[];
-  __shared__ uint64_t hoff[1 << (11 - kMinLowBits)];
+  __shared__ uint64_t hoff[1 << (11 - kMinLowBitsL2)];
   __shared__ DiagS D;
   const uint32_t M = 1u << P.m;
   const uint64_t ntiles = 1ull << __popcll(P.outer_mask);
@@ -283,7 +283,7 @@ __global__ void __launch_bounds__(kFT) k_bpass(double2* __restrict__ psi,
                                                const double* __restrict__ theta,
                                                double* __restrict__ partial) {
   extern __shared__ double2 smem[];
-  __shared__ uint64_t hoff[1 << (11 - kMinLowBits)];
+  __shared__ uint64_t hoff[1 << (11 - kMinLowBitsL2)];
   __shared__ DiagS D;
   __shared__ double red[kFT / 32];
   const uint32_t M = 1u << P.m;
@@ -397,7 +397,7 @@ __global__ void __launch_bounds__(kFT) k_gpass(const double2* __restrict__ psi,
                                                const FItem* __restrict__ items,
                                                double* __restrict__ partial) {
   extern __shared__ double2 smem[];
-  __shared__ uint64_t hoff[1 << (11 - kMinLowBits)];
+  __shared__ uint64_t hoff[1 << (11 - kMinLowBitsL2)];
   __shared__ double red[kFT / 32];
   const uint32_t M = 1u << P.m;
   double2* tp = smem;

@@ -90,8 +90,13 @@ static_assert(sizeof(Seg) == 16, "Seg layout");
 constexpr int kMaxPerm = 32;
 // Gradient slots per fused pass (and RZ gates per diagonal item).
 constexpr int kMaxSlotsDev = 16;
-// Lowest contiguous bits every fused tile includes (runs of 2^kMinLowBits amplitudes).
+// Lowest contiguous bits every fused tile includes (runs of 2^kMinLowBits amplitudes, 256 B),
+// so that tiles of an HBM-resident state move in long DRAM bursts.  A state small enough for
+// psi and lambda to stay in L2 (n <= kL2Qubits) needs only 32-byte sectors: its tiles include
+// kMinLowBitsL2 low bits, which leaves more of the tile's bits for gate wires (fewer passes).
 constexpr int kMinLowBits = 4;
+constexpr int kMinLowBitsL2 = 2;
+constexpr int kL2Qubits = 21;
 
 // A fused pass of the single-state path: every item of the pass acts inside one "tile" of
 // 2^m amplitudes (the basis-index bits in tile_mask, which always include the c lowest bits,
