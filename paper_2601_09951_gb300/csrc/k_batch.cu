@@ -618,15 +618,28 @@ __device__ void run_instance(const BatchArgs& a, int idx, const Team& T, TeamS& 
         cn = a.tables[Gn.toff];
         Gnn = grec(groups[g + 2 < ng ? g + 2 : ng - 1]);
         const uint32_t x = G.x, zu = G.zu;
-        if (G.cls >= 4) {
-          const int cls = G.cls - 4;
+        if (G.cls == 4) {
+          // real coefficient: acc += s c psi[k ^ x], s = (-1)^popc(k & zu) as a sign bit
 #pragma unroll
           for (int u = 0; u < kHU; ++u) {
             const uint32_t k = k0 + u * TS;
             if (k < N) {
-              double2 f = c;
-              if (__popc(k & zu) & 1) f = make_double2(dneg(f.x), dneg(f.y));
-              group_madd(cls, f, psi[k ^ x], acc[u]);
+              const double2 v = psi[k ^ x];
+              const double f = (__popc(k & zu) & 1) ? dneg(c.x) : c.x;
+              acc[u].x = fma(f, v.x, acc[u].x);
+              acc[u].y = fma(f, v.y, acc[u].y);
+            }
+          }
+        } else if (G.cls == 5) {
+          // imaginary coefficient i c: acc += s (-c v.y, c v.x)
+#pragma unroll
+          for (int u = 0; u < kHU; ++u) {
+            const uint32_t k = k0 + u * TS;
+            if (k < N) {
+              const double2 v = psi[k ^ x];
+              const double f = (__popc(k & zu) & 1) ? dneg(c.y) : c.y;
+              acc[u].x = fma(dneg(f), v.y, acc[u].x);
+              acc[u].y = fma(f, v.x, acc[u].y);
             }
           }
         } else {
