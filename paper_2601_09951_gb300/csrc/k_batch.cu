@@ -597,6 +597,9 @@ __device__ void run_instance(const BatchArgs& a, int idx, const Team& T, TeamS& 
     // group-record load per thread per group.
     double e = 0.0;
     constexpr int kHU = 16;
+    // u runs over the thread's amplitudes k = k0 + u TS: nu of them (N <= kHU TS in every
+    // class, so one k0 per thread)
+    const int nu = N >= (uint32_t)TS ? (int)(N >> T.log_size) : 1;
     for (uint32_t k0 = tid; k0 < N; k0 += kHU * TS) {
       double2 acc[kHU];
 #pragma unroll
@@ -622,8 +625,9 @@ __device__ void run_instance(const BatchArgs& a, int idx, const Team& T, TeamS& 
           // real coefficient: acc += s c psi[k ^ x], s = (-1)^popc(k & zu) as a sign bit
 #pragma unroll
           for (int u = 0; u < kHU; ++u) {
+            if (u >= nu) break;
             const uint32_t k = k0 + u * TS;
-            if (k < N) {
+            {
               const double2 v = psi[k ^ x];
               const double f = (__popc(k & zu) & 1) ? dneg(c.x) : c.x;
               acc[u].x = fma(f, v.x, acc[u].x);
@@ -634,8 +638,9 @@ __device__ void run_instance(const BatchArgs& a, int idx, const Team& T, TeamS& 
           // imaginary coefficient i c: acc += s (-c v.y, c v.x)
 #pragma unroll
           for (int u = 0; u < kHU; ++u) {
+            if (u >= nu) break;
             const uint32_t k = k0 + u * TS;
-            if (k < N) {
+            {
               const double2 v = psi[k ^ x];
               const double f = (__popc(k & zu) & 1) ? dneg(c.y) : c.y;
               acc[u].x = fma(dneg(f), v.y, acc[u].x);
@@ -653,23 +658,61 @@ __device__ void run_instance(const BatchArgs& a, int idx, const Team& T, TeamS& 
 #pragma unroll
           for (int b = 0; b < 4; ++b)
             d[b] = ((zh >> b) & 1u) << (sh + __popc(zh & ((1u << b) - 1u)));
+          // a real or imaginary table is read one component at a time (8 bytes per entry)
+          const double* tab = reinterpret_cast<const double*>(a.tables + G.toff);
+          if (G.cls == 0) {
 #pragma unroll
-          for (int u = 0; u < kHU; ++u) {
-            const uint32_t k = k0 + u * TS;
-            if (k < N) {
-              uint32_t ti = base;
+            for (int u = 0; u < kHU; ++u) {
+              if (u >= nu) break;
+              const uint32_t k = k0 + u * TS;
+              {
+                uint32_t ti = base;
 #pragma unroll
-              for (int b = 0; b < 4; ++b)
-                if ((u >> b) & 1) ti += d[b];
-              group_madd(G.cls, a.tables[G.toff + ti], psi[k ^ x], acc[u]);
+                for (int b = 0; b < 4; ++b)
+                  if ((u >> b) & 1) ti += d[b];
+                const double f = tab[2 * ti];
+                const double2 v = psi[k ^ x];
+                acc[u].x = fma(f, v.x, acc[u].x);
+                acc[u].y = fma(f, v.y, acc[u].y);
+              }
+            }
+          } else if (G.cls == 1) {
+#pragma unroll
+            for (int u = 0; u < kHU; ++u) {
+              if (u >= nu) break;
+              const uint32_t k = k0 + u * TS;
+              {
+                uint32_t ti = base;
+#pragma unroll
+                for (int b = 0; b < 4; ++b)
+                  if ((u >> b) & 1) ti += d[b];
+                const double f = tab[2 * ti + 1];
+                const double2 v = psi[k ^ x];
+                acc[u].x = fma(dneg(f), v.y, acc[u].x);
+                acc[u].y = fma(f, v.x, acc[u].y);
+              }
+            }
+          } else {
+#pragma unroll
+            for (int u = 0; u < kHU; ++u) {
+              if (u >= nu) break;
+              const uint32_t k = k0 + u * TS;
+              {
+                uint32_t ti = base;
+#pragma unroll
+                for (int b = 0; b < 4; ++b)
+                  if ((u >> b) & 1) ti += d[b];
+                group_madd(2, a.tables[G.toff + ti], psi[k ^ x], acc[u]);
+              }
             }
           }
         }
       }
 #pragma unroll
       for (int u = 0; u < kHU; ++u) {
+        if (u >= nu) break;
         const uint32_t k = k0 + u * TS;
-        if (k < N) {
+        {
           lam[k] = acc[u];
           const double2 p = psi[k];
           e = fma(p.x, acc[u].x, e);
