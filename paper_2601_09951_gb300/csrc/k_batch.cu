@@ -788,10 +788,14 @@ __device__ void run_instance(const BatchArgs& a, int idx, const Team& T, TeamS& 
         const int nhb = n - T.log_size;
         double W = 0.0, hb[kHB] = {0.0, 0.0, 0.0, 0.0};
         double2 lr[kHU];
+        // the thread's amplitudes are k = tid + u TS for u < nu (index bit log_size + q is
+        // bit q of u)
+        const int nu = N >= (uint32_t)TS ? (int)(N >> T.log_size) : ((uint32_t)tid < N ? 1 : 0);
 #pragma unroll
         for (int u = 0; u < kHU; ++u) {
+          if (u >= nu) break;
           const uint32_t k = tid + u * TS;
-          if (k < N) {
+          {
             const uint32_t src = perm_map(S, k);
             const double2 pk = psi[src];
             double2 lk = lam[src];
@@ -799,7 +803,7 @@ __device__ void run_instance(const BatchArgs& a, int idx, const Team& T, TeamS& 
             W += w;
 #pragma unroll
             for (int q = 0; q < kHB; ++q)
-              if (q < nhb) hb[q] += ((k >> (T.log_size + q)) & 1u) ? dneg(w) : w;
+              if (q < nhb) hb[q] += ((u >> q) & 1) ? dneg(w) : w;
             const double2 ph = cmul(S.th[k >> hl], S.tl[k & lmask]);
             lk = cmul_conj(lk, ph);
             if (ncz && cz_sign(S, ncz, k)) lk = make_double2(dneg(lk.x), dneg(lk.y));
@@ -811,8 +815,8 @@ __device__ void run_instance(const BatchArgs& a, int idx, const Team& T, TeamS& 
         async_copy(T, psi, ck + (size_t)sg.ckpt * N, N);
 #pragma unroll
         for (int u = 0; u < kHU; ++u) {
-          const uint32_t k = tid + u * TS;
-          if (k < N) lam[k] = lr[u];
+          if (u >= nu) break;
+          lam[tid + u * TS] = lr[u];
         }
 #pragma unroll
         for (int g = 0; g < kM; ++g) {
