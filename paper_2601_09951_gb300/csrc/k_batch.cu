@@ -18,6 +18,8 @@
 //   * several gradients are reduced at once with a transposed warp reduction.
 // Every sum runs in a fixed order that does not depend on which CTA or SM ran the instance,
 // so an instance's result is bit-identical alone or in any batch.
+#include <type_traits>
+
 #include "launch.h"
 #include "svqe_internal.cuh"
 
@@ -600,126 +602,133 @@ __device__ void run_instance(const BatchArgs& a, int idx, const Team& T, TeamS& 
     // u runs over the thread's amplitudes k = k0 + u TS: nu of them (N <= kHU TS in every
     // class, so one k0 per thread)
     const int nu = N >= (uint32_t)TS ? (int)(N >> T.log_size) : 1;
-    for (uint32_t k0 = tid; k0 < N; k0 += kHU * TS) {
-      double2 acc[kHU];
-#pragma unroll
-      for (int u = 0; u < kHU; ++u) acc[u] = make_double2(0.0, 0.0);
-      // group records are loaded two groups ahead and the first table entry (a single-term
-      // group's coefficient) one group ahead, so neither load waits in the loop
-      const int ng = I.n_groups;
-      GRec Gn, Gnn;
-      double2 cn = make_double2(0.0, 0.0);
-      if (ng > 0) {
-        Gn = grec(groups[0]);
-        Gnn = grec(groups[ng > 1 ? 1 : 0]);
-        cn = a.tables[Gn.toff];
-      }
-      for (int g = 0; g < ng; ++g) {
-        const GRec G = Gn;
-        const double2 c = cn;
-        Gn = Gnn;
-        cn = a.tables[Gn.toff];
-        Gnn = grec(groups[g + 2 < ng ? g + 2 : ng - 1]);
-        const uint32_t x = G.x, zu = G.zu;
-        if (G.cls == 4) {
-          // real coefficient: acc += s c psi[k ^ x], s = (-1)^popc(k & zu) as a sign bit
-#pragma unroll
-          for (int u = 0; u < kHU; ++u) {
-            if (u >= nu) break;
-            const uint32_t k = k0 + u * TS;
-            {
-              const double2 v = psi[k ^ x];
-              const double f = (__popc(k & zu) & 1) ? dneg(c.x) : c.x;
-              acc[u].x = fma(f, v.x, acc[u].x);
-              acc[u].y = fma(f, v.y, acc[u].y);
-            }
-          }
-        } else if (G.cls == 5) {
-          // imaginary coefficient i c: acc += s (-c v.y, c v.x)
-#pragma unroll
-          for (int u = 0; u < kHU; ++u) {
-            if (u >= nu) break;
-            const uint32_t k = k0 + u * TS;
-            {
-              const double2 v = psi[k ^ x];
-              const double f = (__popc(k & zu) & 1) ? dneg(c.y) : c.y;
-              acc[u].x = fma(dneg(f), v.y, acc[u].x);
-              acc[u].y = fma(f, v.x, acc[u].y);
-            }
-          }
-        } else {
-          // table index pext(k, zu) with k = k0 + u TS (k0 < TS: N <= kHU TS in every class):
-          // the bits of zu below log_size give a per-thread base, and each set bit b of u adds
-          // d[b] (zero unless bit log_size + b is in zu)
-          const uint32_t zl = zu & (uint32_t)(TS - 1), zh = zu >> T.log_size;
-          const uint32_t base = pext32(k0, zl);
-          const int sh = __popc(zl);
-          uint32_t d[4];
-#pragma unroll
-          for (int b = 0; b < 4; ++b)
-            d[b] = ((zh >> b) & 1u) << (sh + __popc(zh & ((1u << b) - 1u)));
-          // a real or imaginary table is read one component at a time (8 bytes per entry)
-          const double* tab = reinterpret_cast<const double*>(a.tables + G.toff);
-          if (G.cls == 0) {
-#pragma unroll
+    // the group loop runs in two forms: every slot u valid (FULL, the common case for the
+    // larger registers), or stopping at u = nu
+    auto hpsi = [&](auto full_tag) {
+      constexpr bool FULL = decltype(full_tag)::value;
+      for (uint32_t k0 = tid; k0 < N; k0 += kHU * TS) {
+        double2 acc[kHU];
+  #pragma unroll
+        for (int u = 0; u < kHU; ++u) acc[u] = make_double2(0.0, 0.0);
+        // group records are loaded two groups ahead and the first table entry (a single-term
+        // group's coefficient) one group ahead, so neither load waits in the loop
+        const int ng = I.n_groups;
+        GRec Gn, Gnn;
+        double2 cn = make_double2(0.0, 0.0);
+        if (ng > 0) {
+          Gn = grec(groups[0]);
+          Gnn = grec(groups[ng > 1 ? 1 : 0]);
+          cn = a.tables[Gn.toff];
+        }
+        for (int g = 0; g < ng; ++g) {
+          const GRec G = Gn;
+          const double2 c = cn;
+          Gn = Gnn;
+          cn = a.tables[Gn.toff];
+          Gnn = grec(groups[g + 2 < ng ? g + 2 : ng - 1]);
+          const uint32_t x = G.x, zu = G.zu;
+          if (G.cls == 4) {
+            // real coefficient: acc += s c psi[k ^ x], s = (-1)^popc(k & zu) as a sign bit
+  #pragma unroll
             for (int u = 0; u < kHU; ++u) {
-              if (u >= nu) break;
+              if (!FULL && u >= nu) break;
               const uint32_t k = k0 + u * TS;
               {
-                uint32_t ti = base;
-#pragma unroll
-                for (int b = 0; b < 4; ++b)
-                  if ((u >> b) & 1) ti += d[b];
-                const double f = tab[2 * ti];
                 const double2 v = psi[k ^ x];
+                const double f = (__popc(k & zu) & 1) ? dneg(c.x) : c.x;
                 acc[u].x = fma(f, v.x, acc[u].x);
                 acc[u].y = fma(f, v.y, acc[u].y);
               }
             }
-          } else if (G.cls == 1) {
-#pragma unroll
+          } else if (G.cls == 5) {
+            // imaginary coefficient i c: acc += s (-c v.y, c v.x)
+  #pragma unroll
             for (int u = 0; u < kHU; ++u) {
-              if (u >= nu) break;
+              if (!FULL && u >= nu) break;
               const uint32_t k = k0 + u * TS;
               {
-                uint32_t ti = base;
-#pragma unroll
-                for (int b = 0; b < 4; ++b)
-                  if ((u >> b) & 1) ti += d[b];
-                const double f = tab[2 * ti + 1];
                 const double2 v = psi[k ^ x];
+                const double f = (__popc(k & zu) & 1) ? dneg(c.y) : c.y;
                 acc[u].x = fma(dneg(f), v.y, acc[u].x);
                 acc[u].y = fma(f, v.x, acc[u].y);
               }
             }
           } else {
-#pragma unroll
-            for (int u = 0; u < kHU; ++u) {
-              if (u >= nu) break;
-              const uint32_t k = k0 + u * TS;
-              {
-                uint32_t ti = base;
-#pragma unroll
-                for (int b = 0; b < 4; ++b)
-                  if ((u >> b) & 1) ti += d[b];
-                group_madd(2, a.tables[G.toff + ti], psi[k ^ x], acc[u]);
+            // table index pext(k, zu) with k = k0 + u TS (k0 < TS: N <= kHU TS in every class):
+            // the bits of zu below log_size give a per-thread base, and each set bit b of u adds
+            // d[b] (zero unless bit log_size + b is in zu)
+            const uint32_t zl = zu & (uint32_t)(TS - 1), zh = zu >> T.log_size;
+            const uint32_t base = pext32(k0, zl);
+            const int sh = __popc(zl);
+            uint32_t d[4];
+  #pragma unroll
+            for (int b = 0; b < 4; ++b)
+              d[b] = ((zh >> b) & 1u) << (sh + __popc(zh & ((1u << b) - 1u)));
+            // a real or imaginary table is read one component at a time (8 bytes per entry)
+            const double* tab = reinterpret_cast<const double*>(a.tables + G.toff);
+            if (G.cls == 0) {
+  #pragma unroll
+              for (int u = 0; u < kHU; ++u) {
+                if (!FULL && u >= nu) break;
+                const uint32_t k = k0 + u * TS;
+                {
+                  uint32_t ti = base;
+  #pragma unroll
+                  for (int b = 0; b < 4; ++b)
+                    if ((u >> b) & 1) ti += d[b];
+                  const double f = tab[2 * ti];
+                  const double2 v = psi[k ^ x];
+                  acc[u].x = fma(f, v.x, acc[u].x);
+                  acc[u].y = fma(f, v.y, acc[u].y);
+                }
+              }
+            } else if (G.cls == 1) {
+  #pragma unroll
+              for (int u = 0; u < kHU; ++u) {
+                if (!FULL && u >= nu) break;
+                const uint32_t k = k0 + u * TS;
+                {
+                  uint32_t ti = base;
+  #pragma unroll
+                  for (int b = 0; b < 4; ++b)
+                    if ((u >> b) & 1) ti += d[b];
+                  const double f = tab[2 * ti + 1];
+                  const double2 v = psi[k ^ x];
+                  acc[u].x = fma(dneg(f), v.y, acc[u].x);
+                  acc[u].y = fma(f, v.x, acc[u].y);
+                }
+              }
+            } else {
+  #pragma unroll
+              for (int u = 0; u < kHU; ++u) {
+                if (!FULL && u >= nu) break;
+                const uint32_t k = k0 + u * TS;
+                {
+                  uint32_t ti = base;
+  #pragma unroll
+                  for (int b = 0; b < 4; ++b)
+                    if ((u >> b) & 1) ti += d[b];
+                  group_madd(2, a.tables[G.toff + ti], psi[k ^ x], acc[u]);
+                }
               }
             }
           }
         }
-      }
-#pragma unroll
-      for (int u = 0; u < kHU; ++u) {
-        if (u >= nu) break;
-        const uint32_t k = k0 + u * TS;
-        {
-          lam[k] = acc[u];
-          const double2 p = psi[k];
-          e = fma(p.x, acc[u].x, e);
-          e = fma(p.y, acc[u].y, e);
+  #pragma unroll
+        for (int u = 0; u < kHU; ++u) {
+          if (!FULL && u >= nu) break;
+          const uint32_t k = k0 + u * TS;
+          {
+            lam[k] = acc[u];
+            const double2 p = psi[k];
+            e = fma(p.x, acc[u].x, e);
+            e = fma(p.y, acc[u].y, e);
+          }
         }
       }
-    }
+    };
+    if (nu == kHU) hpsi(std::true_type{});
+    else hpsi(std::false_type{});
     const double E = team_sum(T, S, e);
     T.sync();
 
