@@ -319,16 +319,34 @@ __device__ __forceinline__ void lop_pass(const Team& T, double2* v, uint32_t N, 
   }
 }
 
-// Two staged layer gates on distinct bits in one pass (as op_pass2).  If ckout is set, the
-// amplitudes are also stored there unchanged first: the pass doubles as the checkpoint copy.
-__device__ __forceinline__ void lop_pass2(const Team& T, double2* v, uint32_t N, const LOp& o1,
-                                          const LOp& o2, bool inv, double2* ckout) {
+// One layer gate on a pair, with the rotation (and its inverse, for RX) prepared: RY rotates
+// (re x, re y) and (im x, im y) by R(phi); RX rotates (re x, im y) by R(-phi) and (im x, re y)
+// by R(phi).
+template <bool ROTX>
+__device__ __forceinline__ void layer_pair(const Rot& r, const Rot& m, double2& x, double2& y) {
+  if (ROTX) {
+    rot_apply(m, x.x, y.y);
+    rot_apply(r, x.y, y.x);
+  } else {
+    rot_apply(r, x.x, y.x);
+    rot_apply(r, x.y, y.y);
+  }
+}
+
+// Two staged layer gates on distinct bits in one pass: each thread takes the four amplitudes of
+// a block (both bits 0, either, both 1), rotates them for the first gate, then for the second,
+// in registers (inverse: inverted, in reverse order).  A layer is all RY or all RX.  If ckout
+// is set, the amplitudes are also stored there unchanged first: the pass doubles as the
+// checkpoint copy.
+template <bool ROTX>
+__device__ __forceinline__ void lop_pass2_k(const Team& T, double2* v, uint32_t N, const LOp& o1,
+                                            const LOp& o2, bool inv, double2* ckout) {
   const uint32_t b1 = 1u << o1.bit, b2 = 1u << o2.bit;
   uint8_t sb[2];
   sb[0] = (uint8_t)min(o1.bit, o2.bit);
   sb[1] = (uint8_t)max(o1.bit, o2.bit);
-  const Rot r1 = o1.r, r2 = o2.r;
-  const int t1 = o1.type, t2 = o2.type;
+  const Rot r1 = inv ? rot_inverse(o1.r) : o1.r, r2 = inv ? rot_inverse(o2.r) : o2.r;
+  const Rot m1 = rot_inverse(r1), m2 = rot_inverse(r2);
   for (uint32_t p = T.rank; p < (N >> 2); p += T.size) {
     const uint32_t i = insert_zeros32(p, sb, 2);
     double2 a = v[i], b = v[i | b1], c = v[i | b2], d = v[i | b1 | b2];
@@ -339,21 +357,27 @@ __device__ __forceinline__ void lop_pass2(const Team& T, double2* v, uint32_t N,
       ckout[i | b1 | b2] = d;
     }
     if (!inv) {
-      pair_apply(t1, r1, false, a, b);
-      pair_apply(t1, r1, false, c, d);
-      pair_apply(t2, r2, false, a, c);
-      pair_apply(t2, r2, false, b, d);
+      layer_pair<ROTX>(r1, m1, a, b);
+      layer_pair<ROTX>(r1, m1, c, d);
+      layer_pair<ROTX>(r2, m2, a, c);
+      layer_pair<ROTX>(r2, m2, b, d);
     } else {
-      pair_apply(t2, r2, true, a, c);
-      pair_apply(t2, r2, true, b, d);
-      pair_apply(t1, r1, true, a, b);
-      pair_apply(t1, r1, true, c, d);
+      layer_pair<ROTX>(r2, m2, a, c);
+      layer_pair<ROTX>(r2, m2, b, d);
+      layer_pair<ROTX>(r1, m1, a, b);
+      layer_pair<ROTX>(r1, m1, c, d);
     }
     v[i] = a;
     v[i | b1] = b;
     v[i | b2] = c;
     v[i | b1 | b2] = d;
   }
+}
+
+__device__ __forceinline__ void lop_pass2(const Team& T, double2* v, uint32_t N, const LOp& o1,
+                                          const LOp& o2, bool inv, double2* ckout) {
+  if (o1.type == SV_GATE_RX) lop_pass2_k<true>(T, v, N, o1, o2, inv, ckout);
+  else lop_pass2_k<false>(T, v, N, o1, o2, inv, ckout);
 }
 
 // Build the diagonal segment's half tables: th[hi] * tl[lo] = prod_RZ e^{-i phi s(k)}, and
@@ -856,15 +880,23 @@ __device__ void run_instance(const BatchArgs& a, int idx, const Team& T, TeamS& 
           sb[0] = (uint8_t)min(o1.bit, o2.bit);
           sb[1] = (uint8_t)max(o1.bit, o2.bit);
           double a1 = 0.0, a2 = 0.0;
-          for (uint32_t p = tid; p < (N >> 2); p += TS) {
-            const uint32_t i = insert_zeros32(p, sb, 2);
-            const double2 pa = psi[i], pb = psi[i | b1], pc = psi[i | b2], pd = psi[i | b1 | b2];
-            const double2 la = lam[i], lb = lam[i | b1], lc = lam[i | b2], ld = lam[i | b1 | b2];
-            pair_grad_acc(o1.type, la, lb, pa, pb, a1);
-            pair_grad_acc(o1.type, lc, ld, pc, pd, a1);
-            pair_grad_acc(o2.type, la, lc, pa, pc, a2);
-            pair_grad_acc(o2.type, lb, ld, pb, pd, a2);
-          }
+          // a layer is all RY or all RX: one loop per kind, no per-pair dispatch
+          auto grads = [&](auto kind_tag) {
+            constexpr int KIND = decltype(kind_tag)::value;
+            for (uint32_t p = tid; p < (N >> 2); p += TS) {
+              const uint32_t i = insert_zeros32(p, sb, 2);
+              const double2 pa = psi[i], pb = psi[i | b1], pc = psi[i | b2],
+                            pd = psi[i | b1 | b2];
+              const double2 la = lam[i], lb = lam[i | b1], lc = lam[i | b2],
+                            ld = lam[i | b1 | b2];
+              pair_grad_acc(KIND, la, lb, pa, pb, a1);
+              pair_grad_acc(KIND, lc, ld, pc, pd, a1);
+              pair_grad_acc(KIND, la, lc, pa, pc, a2);
+              pair_grad_acc(KIND, lb, ld, pb, pd, a2);
+            }
+          };
+          if (o1.type == SV_GATE_RX) grads(std::integral_constant<int, SV_GATE_RX>{});
+          else grads(std::integral_constant<int, SV_GATE_RY>{});
 #pragma unroll
           for (int q = 0; q < kM; ++q) {
             if (q == g) v[q] = a1;
