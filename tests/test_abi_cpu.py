@@ -67,6 +67,18 @@ def test_bad_qubit_count_is_einval_without_touching_the_gpu():
         assert e.value.status == svqe.SV_EINVAL
 
 
+def test_context_options_reject_null_handles():
+    """sv_set_checkpoint_bytes, sv_set_autotune and sv_tile_bits answer SV_EINVAL for a NULL
+    handle (or output) without touching the device."""
+    import ctypes
+    L = svqe.lib()
+    assert L.sv_set_checkpoint_bytes(None, 1 << 30) == svqe.SV_EINVAL
+    assert L.sv_set_autotune(None, 1) == svqe.SV_EINVAL
+    t = ctypes.c_int32(0)
+    assert L.sv_tile_bits(None, ctypes.byref(t)) == svqe.SV_EINVAL
+    assert L.sv_tile_bits(None, None) == svqe.SV_EINVAL
+
+
 def _apply_lowered(n, lowered, psi):
     x, zu, cls, toff, table = lowered
     out = np.zeros_like(psi)
