@@ -40,7 +40,7 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", default="batch",
-                    choices=["batch", "serve", "kernels", "single", "h2", "classes"],
+                    choices=["batch", "serve", "kernels", "single", "h2", "classes", "tfim"],
                     help="batch: the batched evaluation step (default); serve: the request "
                          "loop (latency percentiles), printed as its own JSON line")
     ap.add_argument("--requests", type=int, default=300)
@@ -427,6 +427,62 @@ def per_circuit(insts, sample):
             "launches_per_eval": launches / len(prepared)}
 
 
+def run_tfim(args):
+    """The paper's CPU vs GPU scaling study shape (Sec. 5.2, Table 3): a transverse-field Ising
+    chain at 4..26 qubits under a 2-layer hardware-efficient ansatz.  Per n, one line: the
+    single-state energy + adjoint gradient (CUDA events), 100 gradient-descent steps through
+    vqe_step (host wall time, energies copied back), and for n <= 14 the oracle's
+    parameter-shift evaluation on one host core.  The paper's times (PennyLane, EPYC core vs
+    H100, unstated iteration count) are context only."""
+    import torch
+    torch.cuda.set_device(0)
+    from paper_2601_09951_gb300 import build as libbuild
+    libbuild.build()
+    from paper_2601_09951_gb300 import svqe
+    from paper_2601_09951_gb300 import workloads as W
+    import oracle
+    paper = {4: (8.33, 0.79), 8: (6.54, 1.07), 12: (4.24, 1.20), 14: (9.10, 0.90),
+             16: (5.67, 0.85), 18: (12.03, 0.84), 20: (46.77, 1.08), 22: (161.07, 2.21),
+             24: (478.73, 5.87), 26: (1425.06, 17.71)}
+    oracle.set_threads(1)
+    for n in sorted(paper):
+        inst = W.tfim_instance(n)
+        stream = torch.cuda.Stream()
+        ctx = svqe.Context(n, stream=stream.cuda_stream)
+        ctx.init_reference(0)
+        H = svqe.Ham(ctx, inst["ham"])
+        C = svqe.Circuit(inst["circuit"])
+        th = torch.tensor(np.asarray(inst["theta"]), device="cuda")
+        e = torch.zeros(1, dtype=torch.float64, device="cuda")
+        g = torch.zeros(C.n_params, dtype=torch.float64, device="cuda")
+        call = lambda: ctx.adjoint_grad_dev(C, th.data_ptr(), H, e.data_ptr(), g.data_ptr())
+        call()
+        torch.cuda.synchronize()
+        reps = 20 if n <= 22 else 5
+        t0 = torch.cuda.Event(enable_timing=True)
+        t1 = torch.cuda.Event(enable_timing=True)
+        t0.record(stream)
+        for _ in range(reps):
+            call()
+        t1.record(stream)
+        torch.cuda.synchronize()
+        eval_ms = t0.elapsed_time(t1) / reps
+        w0 = time.perf_counter()
+        _, es = ctx.vqe_step(C, H, np.asarray(inst["theta"]), 0.05, 100)
+        gd_s = time.perf_counter() - w0
+        line = {"metric": "TFIM scaling: energy+gradient ms and 100 GD steps",
+                "n_qubits": n, "state_bytes": 16 << n, "gates": len(C.gates),
+                "eval_ms": eval_ms, "gd100_s": gd_s, "e_first": float(es[0]),
+                "e_last": float(es[-1]),
+                "paper_context_s": {"cpu": paper[n][0], "gpu_h100": paper[n][1]}}
+        if n <= 14:
+            w0 = time.perf_counter()
+            oracle.energy_grad(inst)
+            line["oracle_1core_s_per_eval"] = time.perf_counter() - w0
+        print(json.dumps(line), flush=True)
+        del ctx, H
+
+
 def run_classes(args):
     """Batched-kernel throughput by register size: for each n, a batch of instances of that n
     alone (hardware-efficient ansatz, 5 layers, 275 terms), enough to give every CTA several
@@ -561,7 +617,7 @@ def main():
     if args.workload != "batch":
         if rank == 0:
             {"serve": run_serve, "kernels": run_kernels, "single": run_single,
-             "h2": run_h2, "classes": run_classes}[args.workload](args)
+             "h2": run_h2, "classes": run_classes, "tfim": run_tfim}[args.workload](args)
         return
     import torch
     torch.cuda.set_device(local)

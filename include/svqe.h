@@ -126,7 +126,7 @@ sv_status sv_create(sv_ctx** out, int32_t n_qubits, void* cuda_stream);
 /* Free a context and everything it allocated (NULL is accepted). */
 sv_status sv_destroy(sv_ctx* ctx);
 /* Device memory (bytes) the context may add for psi checkpoints; the default is 0 (psi and
- * lambda only).  Applies to sv_adjoint_grad* and vqe_step on registers of at least 14 qubits.
+ * lambda only).  Applies to sv_adjoint_grad* and vqe_step.
  * A commuting layer is a run of RY (or RX) gates on distinct qubits.  For up to
  * bytes / (2^n * 16) such layers, the forward pass copies psi before the layer into its own
  * buffer.  The adjoint sweep then takes all of the layer's gradients at its end (the
@@ -136,7 +136,7 @@ sv_status sv_destroy(sv_ctx* ctx);
  * the device allows.  A smaller budget frees the buffers beyond it; SV_EINVAL for a NULL
  * handle. */
 sv_status sv_set_checkpoint_bytes(sv_ctx* ctx, uint64_t bytes);
-/* Autotuning of the fused-pass tile size (registers of at least 14 qubits); off by default
+/* Autotuning of the fused-pass tile size; off by default
  * (tiles of 2^11 amplitudes).  When on, the first sv_adjoint_grad* / vqe_step call with a
  * circuit structure not seen before in the process does the following.  Gate types and wires
  * count as structure; angles do not.  It times the forward pass with tiles of 2^9, 2^10 and
@@ -171,8 +171,9 @@ sv_status sv_ham_info(const sv_ham* h, int32_t* n_groups, uint64_t* device_bytes
 sv_status sv_ham_lower(const sv_paulisum* h, int32_t kmax, int32_t* n_groups, int64_t* n_table,
                        uint64_t* x, uint64_t* zu, int32_t* cls, int64_t* toff, double* table);
 
-/* Host-only inspection of the fused-pass plan the single-state path uses for registers of at
- * least 14 qubits (no device work): *n_passes receives the number of shared-memory passes
+/* Host-only inspection of the fused-pass plan the single-state path uses (no device work;
+ * whole-state segments and checkpointed layers, which cut the plan into chunks on the device
+ * path, are not applied here): *n_passes receives the number of shared-memory passes
  * over the state and, if pass_of_gate is not NULL, pass_of_gate[g] the pass that applies gate
  * g (n_gates entries).  Gates keep their relative order whenever they share a qubit.
  * tile_bits <= 0 selects the library's tile size (11 bits). */

@@ -419,14 +419,14 @@ static sv_status plan_circuit(sv_ctx* c, const HostCircuit& hc, int tile_bits) {
     std::vector<int> layer_at(n_ops, -1);
     for (size_t j = 0; j < layers.size(); ++j) layer_at[layers[j].first] = (int)j;
     // diagonal + permutation runs need the third buffer
-    if (!c->scratch && !c->scratch_failed) {
+    if (c->n >= kDpMinQubits && !c->scratch && !c->scratch_failed) {
       if (cudaMalloc((void**)&c->scratch, sb) != cudaSuccess) {
         cudaGetLastError();
         c->scratch = nullptr;
         c->scratch_failed = true;
       }
     }
-    const bool use_dp = c->scratch != nullptr;
+    const bool use_dp = c->scratch != nullptr && c->n >= kDpMinQubits;
     std::vector<uint32_t> tabs;
     auto is_diag = [&](int t) { return t == SV_GATE_RZ || t == SV_GATE_CZ; };
     auto is_perm = [&](int t) { return t == SV_GATE_CNOT || t == SV_GATE_X; };

@@ -38,9 +38,12 @@ cudaError_t launch_gd_update(double* theta, const double* grad, int n, double lr
 
 namespace svqe {
 
-// Fused passes of the single-state path (k_fused.cu).  Tiles of fused_tile_bits() bits;
-// used for registers of at least kFusedMinQubits qubits.
-constexpr int kFusedMinQubits = 14;
+// Fused passes of the single-state path (k_fused.cu).  Tiles of fused_tile_bits() bits (all
+// of the state when it is smaller); used for registers of at least kFusedMinQubits qubits.
+// Whole-state diagonal + permutation segments (k_dp.cu, blocks of 2048 amplitudes) need at
+// least kDpMinQubits.
+constexpr int kFusedMinQubits = 1;
+constexpr int kDpMinQubits = 14;
 int fused_tile_bits();
 cudaError_t fused_prepare();
 cudaError_t launch_fpass(double2* psi, const FPass& P, const FItem* items, const DOp* gops,

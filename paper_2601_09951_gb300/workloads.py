@@ -280,6 +280,28 @@ def hea_single(n, layers=10, n_terms=100, seed=1004):
 
 
 # ----------------------------------------------------------------------------------------
+# Workload 6: the scaling study's transverse-field Ising Hamiltonian (Sec. 5.2, Table 3).
+# ----------------------------------------------------------------------------------------
+def tfim_instance(n, layers=2, J=1.0, h=1.0, seed=1006):
+    """H = -J sum_i Z_i Z_{i+1} - h sum_i X_i on an open chain of n qubits (the paper names
+    its scaling-study Hamiltonian both a sum of Pauli-Z operators and a transverse-field Ising
+    model; the Ising form contains the Z sum).  Ansatz: `layers` layers of RY(all), RZ(all),
+    CNOT ladder from |0..0>; parameters U[-pi, pi] from the seeded stream of n."""
+    rng = _rng(seed, n)
+    circ = hea_circuit(n, layers)
+    theta = rng.uniform(-np.pi, np.pi, size=circ["n_params"])
+    terms = []
+    for i in range(n - 1):
+        x, z = pauli_masks(n, {i: "Z", i + 1: "Z"})
+        terms.append((x, z, -float(J)))
+    for i in range(n):
+        x, z = pauli_masks(n, {i: "X"})
+        terms.append((x, z, -float(h)))
+    return {"name": f"tfim_n{n}_L{layers}", "circuit": circ, "ham": _ham(terms), "ref": 0,
+            "theta": theta}
+
+
+# ----------------------------------------------------------------------------------------
 # Workload 5: serving stream.
 # ----------------------------------------------------------------------------------------
 def serve_stream(n_requests, rate_per_s, seed=1005, max_qubits=24, steps=20):

@@ -192,3 +192,20 @@ def test_malformed_input_is_einval():
     # the context is still usable afterwards
     ctx.init_reference(5)
     assert abs(ctx.get_state()[5] - 1) == 0
+
+
+@pytest.mark.parametrize("n", [5, 9, 15])
+def test_tfim_scaling_workload(n):
+    """The scaling study's transverse-field Ising chain under the 2-layer ansatz: energy and
+    gradient against the oracle (n = 15 runs the fused and whole-state segment path), and a
+    gradient-descent run that lowers the energy."""
+    inst = W.tfim_instance(n)
+    ctx = svqe.Context(n)
+    ctx.init_reference(0)
+    H = svqe.Ham(ctx, inst["ham"])
+    e, g = ctx.adjoint_grad(inst["circuit"], inst["theta"], H)
+    e0, g0 = oracle.energy_grad(inst)
+    assert_energy(e, e0, inst["ham"], inst["name"])
+    assert_grad(g, g0, inst["ham"], inst["name"])
+    _, es = ctx.vqe_step(inst["circuit"], H, inst["theta"], 0.05, 30)
+    assert es[-1] < es[0]

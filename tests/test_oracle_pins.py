@@ -328,3 +328,18 @@ def test_adam_first_step_and_scale_invariance():
     es10, ths10, _ = oracle.adam_trajectory(big, 0.01, 3)
     np.testing.assert_allclose(ths10, ths, atol=1e-7)
     np.testing.assert_allclose(es10, 10 * es, rtol=1e-6, atol=1e-9)
+
+
+def test_tfim_workload_is_the_ising_chain_and_respects_the_variational_bound():
+    """The scaling study's Hamiltonian generator gives -J sum Z_i Z_{i+1} - h sum X_i on an open
+    chain (built here from Kronecker products), and the oracle's energy of its ansatz state
+    lies above the chain's ground energy (exact diagonalisation)."""
+    n, J, h = 5, 1.0, 0.7
+    inst = W.tfim_instance(n, J=J, h=h)
+    want = sum(-J * D.on_qubits(n, {i: D.PZ, i + 1: D.PZ}) for i in range(n - 1))
+    want = want + sum(-h * D.on_qubits(n, {i: D.PX}) for i in range(n))
+    got = D.ham_dense(n, inst["ham"])
+    np.testing.assert_allclose(got, want, atol=1e-14)
+    lam_min = np.linalg.eigvalsh(want)[0]
+    e, _ = oracle.energy_grad(inst)
+    assert e >= lam_min - 1e-12
