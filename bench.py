@@ -389,7 +389,7 @@ def run_single(args):
 
 def per_circuit(insts, sample):
     """The plain one-circuit-per-launch path on the same instances: each instance's energy and
-    adjoint gradient through a single-state context (sv_adjoint_grad_dev: per-gate kernels),
+    adjoint gradient through a single-state context (sv_adjoint_grad_dev: fused passes),
     one after another on one stream, for the first `sample` instances.  evals/s from CUDA
     events; launches per evaluation counted from the op lists."""
     import torch
@@ -406,9 +406,9 @@ def per_circuit(insts, sample):
         th = torch.tensor(np.asarray(inst["theta"], dtype=np.float64), device="cuda")
         g = torch.zeros(max(C.n_params, 1), dtype=torch.float64, device="cuda")
         prepared.append((ctxs[n], C, th, H, g))
-        # init, coefficients, one forward and one adjoint kernel per gate, H psi + sum,
-        # per-op contributions + per-parameter sums
-        launches += 2 * len(C.gates) + 6
+        # init, coefficients, one forward and one backward kernel per fused pass, H psi + sum,
+        # the partials' reset, per-op contributions + per-parameter sums
+        launches += 2 * svqe.circuit_plan(inst["circuit"])[0] + 7
     e = torch.zeros(1, dtype=torch.float64, device="cuda")
     for ctx, C, th, H, g in prepared:
         ctx.adjoint_grad_dev(C, th.data_ptr(), H, e.data_ptr(), g.data_ptr())
