@@ -64,6 +64,26 @@ def dist_env():
     return rank, world, local
 
 
+def replica_indices(rank, instances):
+    """Instances one rank evaluates: rank r takes indices [r*I, (r+1)*I) of the seeded batch,
+    so the ranks' sets are disjoint and together cover the first I*world instances."""
+    return list(range(rank * instances, (rank + 1) * instances))
+
+
+def max_over_ranks(values, dist, device):
+    """Element-wise maximum of per-rank timings (the slowest rank sets the job's time)."""
+    import torch
+    t = torch.tensor(values, dtype=torch.float64, device=device)
+    if dist is not None:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return t.tolist()
+
+
+def whole_job_rate(instances, world, steps, seconds):
+    """Evaluations per second of the whole job: every rank's instances, every step."""
+    return instances * world * steps / seconds
+
+
 def config(args, world):
     return {"workload": f"hea_batch_{args.instances}_n4-12_L2-8_T50-500",
             "instances_per_gpu": args.instances, "qubits": "4-12", "layers": "2-8",
@@ -631,7 +651,7 @@ def main():
     from paper_2601_09951_gb300 import svqe
     from paper_2601_09951_gb300 import workloads as W
 
-    idx = list(range(rank * args.instances, (rank + 1) * args.instances))
+    idx = replica_indices(rank, args.instances)
     insts = W.hea_batch(args.instances * world, seed=args.seed, indices=idx)
     stream = torch.cuda.Stream()
     batch = svqe.Batch(insts, stream=stream.cuda_stream)
@@ -689,12 +709,8 @@ def main():
         barrier()
         e2e_s = time.perf_counter() - t0
 
-    times = torch.tensor([dev_s, e2e_s, wall], dtype=torch.float64, device="cuda")
-    if dist is not None:
-        dist.all_reduce(times, op=dist.ReduceOp.MAX)
-    dev_s, e2e_s, wall = times.tolist()
-    n_total = args.instances * world
-    value = n_total * args.steps / dev_s
+    dev_s, e2e_s, wall = max_over_ranks([dev_s, e2e_s, wall], dist, "cuda")
+    value = whole_job_rate(args.instances, world, args.steps, dev_s)
     if rank != 0:
         if dist is not None:
             dist.destroy_process_group()
@@ -708,7 +724,7 @@ def main():
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic (seeded generator, shapes of the batched workload)",
         "config": config(args, world),
-        "e2e": {"value": n_total * args.steps / e2e_s, "unit": UNIT,
+        "e2e": {"value": whole_job_rate(args.instances, world, args.steps, e2e_s), "unit": UNIT,
                 "h2d_bytes_per_step": int(8 * P), "d2h_bytes_per_step": int(8 * (P + len(insts)))},
         "gpu_launches": args.steps,
         "roofline": {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS,
