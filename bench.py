@@ -257,7 +257,7 @@ def run_serve(args):
     print(json.dumps(line), flush=True)
 
 
-HBM_PEAK_GBS = 6678.2  # measured copy bandwidth (read + write) on the GB300s
+HBM_PEAK_GBS = 6678.2  # measured copy bandwidth (read + write) of a GB300
 
 # dram__bytes_read.sum + dram__bytes_write.sum of one k_batch launch of the default workload,
 # from the ncu capture recorded in profiles/k_batch_hea_batch.md, keyed by a hash of the
@@ -280,13 +280,13 @@ def _peaks():
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
             return float(json.load(f)["hbm_gbs"]), "measured"
     except Exception:
-        return HBM_PEAK_GBS, "measured (copy, recorded in DESIGN.md)"
+        return HBM_PEAK_GBS, "measured copy bandwidth of this GPU model, built in"
 
 
 def run_kernels(args):
     """Per-kernel timing on the single-state path at n qubits (state larger than L2): each
     kernel type through the public API, CUDA events on the context's stream, algorithmic bytes
-    and FP64 flops per amplitude (the per-row figures in the design doc)."""
+    and FP64 flops per amplitude, as listed beside each kernel below."""
     import torch
     torch.cuda.set_device(0)
     from paper_2601_09951_gb300 import build as libbuild

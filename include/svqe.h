@@ -53,7 +53,7 @@ typedef enum {
   SV_ENOMEM = 2,        /* device or host allocation failed, or an HBM budget is exceeded */
   SV_ECUDA = 3,         /* a CUDA call failed; the handle is now unusable */
   SV_ETIMEOUT = 4,      /* a bounded wait ran out */
-  SV_EUNSUPPORTED = 5,  /* valid request this build does not implement */
+  SV_EUNSUPPORTED = 5,  /* valid request the library does not implement */
   SV_EBUSY = 6          /* result not ready yet (serving poll) */
 } sv_status;
 
