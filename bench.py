@@ -283,6 +283,21 @@ def _peaks():
         return HBM_PEAK_GBS, "measured copy bandwidth of this GPU model, built in"
 
 
+def expval_flops_per_amp(ham):
+    """FP64 flops per amplitude of the energy-only kernel (FMA = 2), summed over X-mask groups:
+    the terms at k and k ^ x are conjugate, so each pair is taken once.  A one-term group costs
+    1 DFMA per amplitude; a real or imaginary table 1 DMUL + 2 DFMA per pair, a complex one
+    twice that; the diagonal group 1 DMUL + 2 DFMA per amplitude."""
+    groups = {}  # x -> Y-count parities of its terms (real, imaginary or both)
+    for x, z in zip(np.asarray(ham["x"], np.uint64).tolist(),
+                    np.asarray(ham["z"], np.uint64).tolist()):
+        groups.setdefault(x, []).append(bin(x & z).count("1") & 1)
+    total = 0.0
+    for x, par in groups.items():
+        total += 5 if x == 0 else 2 if len(par) == 1 else 2.5 * len(set(par))
+    return total
+
+
 def run_kernels(args):
     """Per-kernel timing on the single-state path at n qubits (state larger than L2): each
     kernel type through the public API, CUDA events on the context's stream, algorithmic bytes
@@ -334,10 +349,16 @@ def run_kernels(args):
     timed("RZ mid (a2)", lambda: ctx.apply_circuit(c, th), 32, 6)
     c = one(W.CNOT, [mid, low], param=False)
     timed("CNOT (a3)", lambda: ctx.apply_circuit(c, np.zeros(0)), 16, 0)
+    # Wires on bit 0 put one untouched amplitude in every touched 32-byte sector (the DRAM
+    # moves twice the algorithmic bytes); wires above bit 1 do not.
     c = one(W.SINGLE_EXC, [mid, low])
-    timed("SingleExcitation (a4)", lambda: ctx.apply_circuit(c, th), 16, 3)
+    timed("SingleExcitation bit0 (a4)", lambda: ctx.apply_circuit(c, th), 16, 3)
+    c2 = one(W.SINGLE_EXC, [mid, high])
+    timed("SingleExcitation mid/top (a4)", lambda: ctx.apply_circuit(c2, th), 16, 3)
     c = one(W.DOUBLE_EXC, [high, mid, mid + 1, low])
-    timed("DoubleExcitation (a5)", lambda: ctx.apply_circuit(c, th), 4, 0.75)
+    timed("DoubleExcitation bit0 (a5)", lambda: ctx.apply_circuit(c, th), 4, 0.75)
+    c3 = one(W.DOUBLE_EXC, [high, 1, mid, mid + 1])
+    timed("DoubleExcitation mid/top (a5)", lambda: ctx.apply_circuit(c3, th), 4, 0.75)
     layer = W.hea_circuit(n, 1, ring=True)
     lc = svqe.Circuit(layer)
     lth = np.random.default_rng(0).uniform(-3, 3, layer["n_params"])
@@ -348,7 +369,8 @@ def run_kernels(args):
     inst = W.hea_single(n, layers=1, n_terms=100)
     H = svqe.Ham(ctx, inst["ham"])
     G = H.info()[0]
-    timed(f"expval {G} groups (a7)", lambda: ctx.expval(H), 16 * G + 16, 4 * G + 4)
+    timed(f"expval {G} groups (a7)", lambda: ctx.expval(H), 16 * G,
+          expval_flops_per_amp(inst["ham"]))
     c1 = svqe.Circuit(inst["circuit"])
     th1 = np.asarray(inst["theta"])
     e_d = torch.zeros(1, dtype=torch.float64, device="cuda")

@@ -220,6 +220,119 @@ __global__ void __launch_bounds__(kThreads) k_hpsi(const double2* __restrict__ p
   if (threadIdx.x == 0) partial[blockIdx.x] = t;
 }
 
+// Energy only: E = <psi|H|psi> (Eq. 2), H the Pauli sum of Eq. 3 grouped by X mask:
+// E = sum_g sum_k conj(psi[k]) f_g(k) psi[k ^ x_g].
+// A group's operator is Hermitian (its strings carry real coefficients), so f_g(k ^ x_g) is
+// the conjugate of f_g(k) and the terms at k and k ^ x_g are complex conjugates of each other:
+// the sum runs over one member k of each pair (the top bit of x_g clear) and counts
+// 2 Re(conj(psi[k]) f_g(k) psi[k ^ x_g]).  psi is still read once per group, with half the FP64
+// work of the full lambda = H psi product: for a one-term group the sign (-1)^popc(zu & k) is
+// folded into psi[k ^ x_g] by an integer op and the coefficient applied once per group and
+// warp, one DFMA per amplitude.  The diagonal group (x_g = 0) takes k and k + N/2 together, each once.
+// Work unit: one warp, a chunk of min(N/2, 32 kEU) consecutive pair indices of one group
+// (lane l takes pair indices l, l + 32, ...), so the group record and its class are uniform.
+constexpr int kEULog = 2;
+constexpr int kEU = 1 << kEULog;
+
+__device__ __forceinline__ double2 sign_flip(const double2& w, uint32_t sm) {
+  return make_double2(__hiloint2double(__double2hiint(w.x) ^ sm, __double2loint(w.x)),
+                      __hiloint2double(__double2hiint(w.y) ^ sm, __double2loint(w.y)));
+}
+
+__global__ void __launch_bounds__(kThreads, 4) k_expval(const double2* __restrict__ psi, int n,
+                                                        const DGroup* __restrict__ groups,
+                                                        int n_groups,
+                                                        const double2* __restrict__ tables,
+                                                        double* __restrict__ partial) {
+  __shared__ double red[kThreads / 32];
+  const int lane = threadIdx.x & 31;
+  const int h_log = n - 1;  // N/2 pairs per group
+  const int c_log = min(h_log, 5 + kEULog);
+  const int upg_log = h_log - c_log;  // chunks per group (log2)
+  const uint64_t C = 1ull << c_log;
+  const uint64_t units = (uint64_t)n_groups << upg_log;
+  const uint64_t nwarps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+  // Running sum of the current group (scale applied once, when the group changes).
+  double e = 0.0, acc = 0.0, scale = 0.0;
+  int run_g = -1;
+  for (uint64_t unit = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; unit < units;
+       unit += nwarps) {
+    if ((int)(unit >> upg_log) != run_g) {
+      e = fma(scale, acc, e);
+      acc = 0.0;
+      run_g = (int)(unit >> upg_log);
+    }
+    const DGroup G = groups[run_g];
+    const uint64_t c0 = (unit & ((1ull << upg_log) - 1ull)) << c_log;
+    const uint64_t xp = G.x ? G.x : (1ull << h_log);  // partner mask
+    const int h = 63 - __clzll((long long)xp);
+    const uint64_t lo = (1ull << h) - 1ull;
+    // k of slot u: pair index c0 + lane + 32 u with a zero bit inserted at h (recomputed
+    // where needed rather than held in registers).
+    auto kk = [&](int u) {
+      const uint64_t t = c0 + lane + 32 * u;
+      return ((t & ~lo) << 1) | (t & lo);
+    };
+    double2 v[kEU], w[kEU];
+#pragma unroll
+    for (int u = 0; u < kEU; ++u) {
+      if ((uint64_t)(lane + 32 * u) < C) {
+        v[u] = psi[kk(u)];
+        w[u] = psi[kk(u) ^ xp];
+      } else {
+        v[u] = make_double2(0.0, 0.0);
+        w[u] = v[u];
+      }
+    }
+    if (G.x == 0) {
+      // Diagonal: sum Re f(k) |psi[k]|^2 over both members of the (k, k + N/2) pair.
+      scale = 1.0;
+#pragma unroll
+      for (int u = 0; u < kEU; ++u) {
+        double2 f1, f2;
+        group_value(G, kk(u), tables, f1);
+        group_value(G, kk(u) ^ xp, tables, f2);
+        acc = fma(f1.x, fma(v[u].x, v[u].x, v[u].y * v[u].y), acc);
+        acc = fma(f2.x, fma(w[u].x, w[u].x, w[u].y * w[u].y), acc);
+      }
+    } else if (G.cls >= 4) {
+      // One term: f(k) = c (-1)^popc(zu & k), c real (cls 4) or imaginary (cls 5).
+      const double2 c = tables[G.toff];
+      if (G.cls == 4) {
+        scale = 2.0 * c.x;
+#pragma unroll
+        for (int u = 0; u < kEU; ++u) {
+          const double2 ws = sign_flip(w[u], (uint32_t)(__popcll(kk(u) & G.zu) & 1) << 31);
+          acc = fma(v[u].x, ws.x, acc);
+          acc = fma(v[u].y, ws.y, acc);
+        }
+      } else {
+        // Re(i c conj(v) w) = c (v.y w.x - v.x w.y)
+        scale = 2.0 * c.y;
+#pragma unroll
+        for (int u = 0; u < kEU; ++u) {
+          const double2 ws = sign_flip(w[u], (uint32_t)(__popcll(kk(u) & G.zu) & 1) << 31);
+          acc = fma(v[u].y, ws.x, acc);
+          acc = fma(dneg(v[u].x), ws.y, acc);
+        }
+      }
+    } else {
+      // Tabulated f(k): Re(f conj(v) w) = Re f (v.x w.x + v.y w.y) + Im f (v.y w.x - v.x w.y).
+      scale = 2.0;
+#pragma unroll
+      for (int u = 0; u < kEU; ++u) {
+        double2 f;
+        const int cls = group_value(G, kk(u), tables, f);
+        if (cls != 1) acc = fma(f.x, fma(v[u].x, w[u].x, v[u].y * w[u].y), acc);
+        if (cls != 0) acc = fma(f.y, fma(v[u].y, w[u].x, dneg(v[u].x) * w[u].y), acc);
+      }
+    }
+  }
+  e = fma(scale, acc, e);
+  const double t = block_sum(e, red);
+  if (threadIdx.x == 0) partial[blockIdx.x] = t;
+}
+
 __global__ void k_sum(const double* __restrict__ partial, int count, double* __restrict__ out) {
   __shared__ double red[32];
   double v = 0.0;
@@ -315,7 +428,10 @@ cudaError_t launch_adjoint_op(double2* psi, double2* lam, int n, const DOp& op, 
 cudaError_t launch_hpsi(const double2* psi, double2* lam, int n, const DGroup* groups,
                         int n_groups, const double2* tables, double* partial, cudaStream_t s) {
   const uint64_t N = 1ull << n;
-  k_hpsi<<<kRedBlocks, kThreads, 0, s>>>(psi, lam, N, groups, n_groups, tables, partial);
+  if (!lam && partial)
+    k_expval<<<kRedBlocks, kThreads, 0, s>>>(psi, n, groups, n_groups, tables, partial);
+  else
+    k_hpsi<<<kRedBlocks, kThreads, 0, s>>>(psi, lam, N, groups, n_groups, tables, partial);
   return cudaGetLastError();
 }
 

@@ -70,7 +70,7 @@ def test_circuit_state_and_energy(inst_fn):
     assert_energy(ctx.expval(H), oracle.expval(want, n, inst["ham"])[0], inst["ham"])
 
 
-@pytest.mark.parametrize("n", [1, 2, 5, 9, 14])
+@pytest.mark.parametrize("n", [1, 2, 5, 9, 14, 20])
 def test_expval_random_states_and_groups(n):
     rng = np.random.default_rng(200 + n)
     ham = W.random_pauli_sum(rng, n, 150, 0.3, min(6, n), 1.0)
@@ -87,6 +87,63 @@ def test_expval_random_states_and_groups(n):
         psi = _rand_state(n, rng)
         ctx.set_state(psi)
         assert_energy(ctx.expval(H), oracle.expval(psi, n, ham)[0], ham, f"n={n}")
+
+
+# One Hamiltonian per group class of the energy kernel: a one-term diagonal group, a
+# diagonal table, one-term real / imaginary off-diagonal groups, and real, imaginary and
+# complex tables (several strings sharing one X mask).
+_CLASS_CASES = {
+    "Z": [({0: "Z"}, 0.7)],
+    "Z-table": [({0: "Z"}, 0.7), ({1: "Z"}, -0.4), ({0: "Z", 1: "Z"}, 0.25), ({}, 0.1)],
+    "XX": [({0: "X", 1: "X"}, 0.9)],
+    "Y": [({0: "Y"}, -1.3)],
+    "XX+YY": [({0: "X", 1: "X"}, 0.6), ({0: "Y", 1: "Y"}, 0.45)],
+    "XY-YX": [({0: "X", 1: "Y"}, 0.8), ({0: "Y", 1: "X"}, -0.35)],
+    "X+Y": [({0: "X"}, 0.5), ({0: "Y"}, 0.75)],
+}
+
+
+def _ham_of(n, terms, shift):
+    xs, zs, cs = [], [], []
+    for f, c in terms:
+        x, z = W.pauli_masks(n, {(q + shift) % n: p for q, p in f.items()})
+        xs.append(x)
+        zs.append(z)
+        cs.append(c)
+    return {"n": n, "x": np.array(xs, np.uint64), "z": np.array(zs, np.uint64),
+            "coeff": np.array(cs, np.float64)}
+
+
+@pytest.mark.parametrize("case", sorted(_CLASS_CASES))
+@pytest.mark.parametrize("n", [2, 3, 8, 9, 16])
+def test_expval_each_group_class(case, n):
+    """Every class of group, on the top wires, the bottom wires (bit 0) and in between; n = 8
+    is one chunk of pairs per group, n = 16 many."""
+    rng = np.random.default_rng(300 + n)
+    ctx = svqe.Context(n)
+    for shift in sorted({0, n // 2, n - 2}):
+        ham = _ham_of(n, _CLASS_CASES[case], shift)
+        H = svqe.Ham(ctx, ham)
+        psi = _rand_state(n, rng)
+        ctx.set_state(psi)
+        assert_energy(ctx.expval(H), oracle.expval(psi, n, ham)[0], ham,
+                      f"{case} n={n} shift={shift}")
+
+
+@pytest.mark.parametrize("n", [1, 2, 3])
+def test_expval_single_qubit_registers(n):
+    """n = 1: the diagonal group pairs amplitudes 0 and 1; every group is a single pair."""
+    rng = np.random.default_rng(400 + n)
+    ctx = svqe.Context(n)
+    for case in ("Z", "Y", "X+Y"):
+        ham = _ham_of(n, [({q % n: p for q, p in f.items()}, c) for f, c in _CLASS_CASES[case]
+                          if all(q < n for q in f)], 0)
+        if len(ham["x"]) == 0:
+            continue
+        H = svqe.Ham(ctx, ham)
+        psi = _rand_state(n, rng)
+        ctx.set_state(psi)
+        assert_energy(ctx.expval(H), oracle.expval(psi, n, ham)[0], ham, f"{case} n={n}")
 
 
 def _check_adjoint(inst, theta=None):
