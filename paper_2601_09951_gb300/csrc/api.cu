@@ -1102,6 +1102,8 @@ sv_status sv_batch_create(const sv_instance* inst, int32_t n, void* stream, sv_b
              (double)hh.groups.size() * sizeof(DGroup) +
              (double)hh.tables.size() * sizeof(double2) + 3.0 * 8 * hc.n_params + 8 +
              2.0 * n_ckpt * sizeof(double2) * (double)(1u << hc.n);
+    for (const Seg& g : sg)  // saved diagonal + permutation tables, written and read once
+      if (g.kind == SEG_DIAGPERM) bytes += 2.0 * kDpAuxAmps * sizeof(double2);
     BInst& B = bi[i];
     B = BInst{};
     B.n = hc.n;
@@ -1121,7 +1123,7 @@ sv_status sv_batch_create(const sv_instance* inst, int32_t n, void* stream, sv_b
     B.pp_off = (int64_t)pptr.size();
     theta_off += hc.n_params;
     // a CTA's checkpoint region is split evenly among the teams of the instance's class
-    ckpt_slot = std::max<int64_t>(ckpt_slot, ((int64_t)n_ckpt << hc.n) * class_teams(hc.n));
+    ckpt_slot = std::max<int64_t>(ckpt_slot, team_ckpt_amps(n_ckpt, hc.n) * class_teams(hc.n));
     segs.insert(segs.end(), sg.begin(), sg.end());
     // parameter -> ops using it, in op order (CSR)
     std::vector<std::vector<int32_t>> uses(hc.n_params);

@@ -38,27 +38,35 @@ struct LOp {
   int bit;
 };
 
-// Per-team scratch in static shared memory.
+// Per-team scratch in static shared memory.  Its first kDpBlockAmps x 16 bytes (tl .. n_rz)
+// are the tables of a diagonal + permutation segment: the forward pass builds them and saves
+// the block to the segment's auxiliary checkpoint slot, the sweep copies it back.
 struct TeamS {
-  double red[kWarps];
-  double red16[kWarps][kM];
   double2 tl[64];
   double2 th[64];
-  double2 cs[kM];
+  // A run of CNOT/X gates is an affine map of the index bits over GF(2), so its permutation
+  // is P(k) = pt_lo[k & 63] ^ pt_hi[k >> 6] (n <= 12), with pt_lo holding the constant part.
+  uint32_t pt_lo[64];
+  uint32_t pt_hi[64];
   int rz_op[kM];
   int rz_bit[kM];
   uint32_t cz_mask[kM];  // both-bits masks of the segment's CZ gates
   int n_cz;
   int n_rz;
+  int pad[2];
+  // (end of the saved block)
+  double red[kWarps];
+  double red16[kWarps][kM];
+  double2 cs[kM];
   uint32_t pm_lo[kMaxPerm];  // condition and flip masks of a permutation segment's gates
   uint32_t pm_fl[kMaxPerm];
   LOp lop[kM];               // the gates of a commuting layer, staged once per segment
-  // A run of CNOT/X gates is an affine map of the index bits over GF(2), so its permutation
-  // is P(k) = pt_lo[k & 63] ^ pt_hi[k >> 6] (n <= 12), with pt_lo holding the constant part.
-  uint32_t pt_lo[64];
-  uint32_t pt_hi[64];
 };
-
+constexpr int kDpBlockAmps = 173;
+static_assert(offsetof(TeamS, pad) + sizeof(int) * 2 == kDpBlockAmps * sizeof(double2),
+              "diagonal + permutation block layout");
+static_assert(kDpBlockAmps <= kDpAuxAmps, "auxiliary checkpoint slot too small");
+static_assert(sizeof(TeamS) % 16 == 0, "TeamS alignment");
 
 // A team of nw warps running one instance.  Teams of one warp synchronise with __syncwarp,
 // larger teams with named barrier `bar` (barrier 0 is the CTA-wide one).
@@ -72,6 +80,12 @@ struct Team {
     }
   }
 };
+
+// Save the segment's tables (the leading block of S) to its auxiliary slot; plain stores.
+__device__ __forceinline__ void dp_save(const Team& T, const TeamS& S, double2* dst) {
+  const double2* src = reinterpret_cast<const double2*>(&S);
+  for (int k = T.rank; k < kDpBlockAmps; k += T.size) dst[k] = src[k];
+}
 
 // The diagonal and permutation parts of a SEG_DIAGPERM segment.
 __device__ __forceinline__ Seg diag_part(const Seg& sg) {
@@ -517,6 +531,8 @@ __device__ void run_instance(const BatchArgs& a, int idx, const Team& T, TeamS& 
   double* grad = a.grad + I.grad_off;
   const int tid = T.rank;
   const int TS = T.size;
+  // auxiliary checkpoint slots (saved segment tables) after the I.n_ckpt states
+  double2* aux = ck + (size_t)I.n_ckpt * N;
   const int hl = n < 6 ? n : 6;
   const uint32_t lmask = (1u << hl) - 1u;
   const bool per_inst = a.n_steps < 0;
@@ -559,6 +575,7 @@ __device__ void run_instance(const BatchArgs& a, int idx, const Team& T, TeamS& 
         // flips in order)
         diag_setup(T, S, ops, coef, diag_part(sg), n);
         perm_setup(T, S, ops, perm_part(sg), false, N);
+        dp_save(T, S, aux + (size_t)sg.ckpt * kDpAuxAmps);
         const int ncz = S.n_cz;
         double2* c = ck + (size_t)sg.ckpt * N;
         for (uint32_t k = tid; k < N; k += TS) {
@@ -757,6 +774,7 @@ __device__ void run_instance(const BatchArgs& a, int idx, const Team& T, TeamS& 
     T.sync();
 
     // ---------------------------------------------------------------- adjoint sweep
+    int pre_dp = -1;  // segment whose saved tables are already in S
     for (int s = I.n_segs - 1; s >= 0; --s) {
       const Seg sg = segs[s];
       if (sg.kind == SEG_GATES) {
@@ -813,8 +831,15 @@ __device__ void run_instance(const BatchArgs& a, int idx, const Team& T, TeamS& 
         // take the signed bit sums of w_k = Im(conj(lambda) psi) as for SEG_DIAG, and keep the
         // un-phased lambda in registers until every gather of the team is done (at most kHU
         // amplitudes per thread in every team class)
-        const int m = diag_setup(T, S, ops, coef, diag_part(sg), n);
-        perm_setup(T, S, ops, perm_part(sg), false, N);
+        // the tables the forward pass built at the same parameters (already loaded when the
+        // commuting layer after this segment prefetched them)
+        if (pre_dp != s) {
+          async_copy(T, reinterpret_cast<double2*>(&S), aux + (size_t)sg.ckpt * kDpAuxAmps,
+                     kDpBlockAmps);
+          async_wait();
+          T.sync();
+        }
+        const int m = S.n_rz;
         const int ncz = S.n_cz;
         constexpr int kHB = 4;
         constexpr int kHU = 16;
@@ -867,6 +892,13 @@ __device__ void run_instance(const BatchArgs& a, int idx, const Team& T, TeamS& 
         T.sync();
         continue;
       } else if (sg.kind == SEG_RLAYER) {
+        // a diagonal + permutation segment next in the sweep: start reloading its tables now
+        // (this segment does not use that block; its final wait completes the copy)
+        if (sg.split != 1 && s > 0 && segs[s - 1].kind == SEG_DIAGPERM) {
+          async_copy(T, reinterpret_cast<double2*>(&S),
+                     aux + (size_t)segs[s - 1].ckpt * kDpAuxAmps, kDpBlockAmps);
+          pre_dp = s - 1;
+        }
         // gradients of every gate from (psi, lambda) at the layer's end, two gates per pass:
         // each thread reads a block of four amplitudes of psi and lambda and accumulates both
         // gates' pair terms from it

@@ -249,86 +249,85 @@ __global__ void __launch_bounds__(kThreads, 4) k_expval(const double2* __restric
   const int h_log = n - 1;  // N/2 pairs per group
   const int c_log = min(h_log, 5 + kEULog);
   const int upg_log = h_log - c_log;  // chunks per group (log2)
-  const uint64_t C = 1ull << c_log;
+  const uint32_t C = 1u << c_log;
   const uint64_t units = (uint64_t)n_groups << upg_log;
   const uint64_t nwarps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
-  // Running sum of the current group (scale applied once, when the group changes).
-  double e = 0.0, acc = 0.0, scale = 0.0;
-  int run_g = -1;
-  for (uint64_t unit = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; unit < units;
-       unit += nwarps) {
-    if ((int)(unit >> upg_log) != run_g) {
-      e = fma(scale, acc, e);
-      acc = 0.0;
-      run_g = (int)(unit >> upg_log);
-    }
-    const DGroup G = groups[run_g];
-    const uint64_t c0 = (unit & ((1ull << upg_log) - 1ull)) << c_log;
-    const uint64_t xp = G.x ? G.x : (1ull << h_log);  // partner mask
-    const int h = 63 - __clzll((long long)xp);
-    const uint64_t lo = (1ull << h) - 1ull;
-    // k of slot u: pair index c0 + lane + 32 u with a zero bit inserted at h (recomputed
-    // where needed rather than held in registers).
-    auto kk = [&](int u) {
-      const uint64_t t = c0 + lane + 32 * u;
-      return ((t & ~lo) << 1) | (t & lo);
+  const uint64_t umask = (1ull << upg_log) - 1ull;
+  double e = 0.0;
+  uint64_t unit = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  while (unit < units) {
+    // One run of this warp's chunks of group g: the class dispatch and the coefficient are
+    // taken once per run, outside the amplitude loop.
+    const int g = (int)(unit >> upg_log);
+    const uint64_t gend = min(units, (uint64_t)(g + 1) << upg_log);
+    const DGroup G = groups[g];
+    // Indices fit in 32 bits (n <= 31).
+    const uint32_t xp = G.x ? (uint32_t)G.x : (1u << h_log);  // partner mask
+    const uint32_t lo = (1u << (31 - __clz((int)xp))) - 1u;
+    double acc = 0.0;
+    // body(k, psi[k], psi[k ^ xp]) for every pair of the run; k is pair index c0 + lane + 32 u
+    // with a zero bit inserted at the top bit of xp.
+    auto sweep = [&](auto body) {
+      for (; unit < gend; unit += nwarps) {
+        const uint32_t c0 = (uint32_t)((unit & umask) << c_log);
+        uint32_t k[kEU];
+        double2 v[kEU], w[kEU];
+#pragma unroll
+        for (int u = 0; u < kEU; ++u) {
+          const uint32_t t = c0 + lane + 32 * u;
+          k[u] = ((t & ~lo) << 1) | (t & lo);
+          if ((uint32_t)(lane + 32 * u) < C) {
+            v[u] = psi[k[u]];
+            w[u] = psi[k[u] ^ xp];
+          } else {
+            v[u] = make_double2(0.0, 0.0);
+            w[u] = v[u];
+          }
+        }
+#pragma unroll
+        for (int u = 0; u < kEU; ++u) body(k[u], v[u], w[u]);
+      }
     };
-    double2 v[kEU], w[kEU];
-#pragma unroll
-    for (int u = 0; u < kEU; ++u) {
-      if ((uint64_t)(lane + 32 * u) < C) {
-        v[u] = psi[kk(u)];
-        w[u] = psi[kk(u) ^ xp];
-      } else {
-        v[u] = make_double2(0.0, 0.0);
-        w[u] = v[u];
-      }
-    }
+    double scale = 2.0;
     if (G.x == 0) {
-      // Diagonal: sum Re f(k) |psi[k]|^2 over both members of the (k, k + N/2) pair.
+      // Diagonal: Re f(k) |psi[k]|^2 for both members of the (k, k + N/2) pair.
       scale = 1.0;
-#pragma unroll
-      for (int u = 0; u < kEU; ++u) {
+      sweep([&](uint32_t kv, const double2& a, const double2& b) {
         double2 f1, f2;
-        group_value(G, kk(u), tables, f1);
-        group_value(G, kk(u) ^ xp, tables, f2);
-        acc = fma(f1.x, fma(v[u].x, v[u].x, v[u].y * v[u].y), acc);
-        acc = fma(f2.x, fma(w[u].x, w[u].x, w[u].y * w[u].y), acc);
-      }
-    } else if (G.cls >= 4) {
-      // One term: f(k) = c (-1)^popc(zu & k), c real (cls 4) or imaginary (cls 5).
-      const double2 c = tables[G.toff];
-      if (G.cls == 4) {
-        scale = 2.0 * c.x;
-#pragma unroll
-        for (int u = 0; u < kEU; ++u) {
-          const double2 ws = sign_flip(w[u], (uint32_t)(__popcll(kk(u) & G.zu) & 1) << 31);
-          acc = fma(v[u].x, ws.x, acc);
-          acc = fma(v[u].y, ws.y, acc);
-        }
-      } else {
-        // Re(i c conj(v) w) = c (v.y w.x - v.x w.y)
-        scale = 2.0 * c.y;
-#pragma unroll
-        for (int u = 0; u < kEU; ++u) {
-          const double2 ws = sign_flip(w[u], (uint32_t)(__popcll(kk(u) & G.zu) & 1) << 31);
-          acc = fma(v[u].y, ws.x, acc);
-          acc = fma(dneg(v[u].x), ws.y, acc);
-        }
-      }
+        group_value(G, kv, tables, f1);
+        group_value(G, kv ^ xp, tables, f2);
+        acc = fma(f1.x, fma(a.x, a.x, a.y * a.y), acc);
+        acc = fma(f2.x, fma(b.x, b.x, b.y * b.y), acc);
+      });
+    } else if (G.cls == 4) {
+      // One term, f(k) = c (-1)^popc(zu & k) with c real: c s (v.x w.x + v.y w.y).
+      scale = 2.0 * tables[G.toff].x;
+      const uint32_t zu = (uint32_t)G.zu;
+      sweep([&](uint32_t kv, const double2& a, const double2& b) {
+        const double2 bs = sign_flip(b, (uint32_t)(__popc(kv & zu) & 1) << 31);
+        acc = fma(a.x, bs.x, acc);
+        acc = fma(a.y, bs.y, acc);
+      });
+    } else if (G.cls == 5) {
+      // One term with c imaginary: Re(i c s conj(v) w) = c s (v.y w.x - v.x w.y).
+      scale = 2.0 * tables[G.toff].y;
+      const uint32_t zu = (uint32_t)G.zu;
+      sweep([&](uint32_t kv, const double2& a, const double2& b) {
+        const double2 bs = sign_flip(b, (uint32_t)(__popc(kv & zu) & 1) << 31);
+        acc = fma(a.y, bs.x, acc);
+        acc = fma(dneg(a.x), bs.y, acc);
+      });
     } else {
       // Tabulated f(k): Re(f conj(v) w) = Re f (v.x w.x + v.y w.y) + Im f (v.y w.x - v.x w.y).
-      scale = 2.0;
-#pragma unroll
-      for (int u = 0; u < kEU; ++u) {
+      sweep([&](uint32_t kv, const double2& a, const double2& b) {
         double2 f;
-        const int cls = group_value(G, kk(u), tables, f);
-        if (cls != 1) acc = fma(f.x, fma(v[u].x, w[u].x, v[u].y * w[u].y), acc);
-        if (cls != 0) acc = fma(f.y, fma(v[u].y, w[u].x, dneg(v[u].x) * w[u].y), acc);
-      }
+        const int cls = group_value(G, kv, tables, f);
+        if (cls != 1) acc = fma(f.x, fma(a.x, b.x, a.y * b.y), acc);
+        if (cls != 0) acc = fma(f.y, fma(a.y, b.x, dneg(a.x) * b.y), acc);
+      });
     }
+    e = fma(scale, acc, e);
   }
-  e = fma(scale, acc, e);
   const double t = block_sum(e, red);
   if (threadIdx.x == 0) partial[blockIdx.x] = t;
 }

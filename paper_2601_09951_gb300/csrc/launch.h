@@ -148,6 +148,7 @@ struct BatchArgs {
   Rot* coef;               // scratch, one per op
   double* contrib;         // scratch, one per op
   double2* ckpt;           // scratch, ckpt_slot amplitudes per CTA, split evenly among teams
+                           // (team_ckpt_amps per instance)
   int64_t ckpt_slot;
   int64_t smem_amps;       // dynamic shared memory per CTA, in amplitudes
   int* counter;            // work-queue head, zeroed before each launch
@@ -164,6 +165,14 @@ struct BatchArgs {
   int adam_t0;
   double beta1, beta2, eps;
 };
+
+// A team's checkpoint scratch for an instance: n_ckpt states of 2^n amplitudes, then one block
+// of kDpAuxAmps amplitudes per checkpoint slot, where a diagonal + permutation segment keeps
+// the tables its forward pass built (phases, permutation, RZ slots) for the sweep to reload.
+constexpr int kDpAuxAmps = 176;
+inline int64_t team_ckpt_amps(int n_ckpt, int n) {
+  return (int64_t)n_ckpt * ((int64_t(1) << n) + kDpAuxAmps);
+}
 
 // Threads per CTA of the batched kernel and its dynamic shared memory for nmax qubits.
 constexpr int kBatchThreads = 256;

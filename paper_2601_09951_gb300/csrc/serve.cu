@@ -38,7 +38,7 @@ namespace svqe {
 namespace {
 
 constexpr int64_t kUnit = 768;                 // lcm of 48, 32, 24, 16, 8, 4 bytes
-constexpr int64_t kCkptAmpsPerCta = 32 * 4096;  // checkpoint capacity of one CTA
+constexpr int64_t kCkptAmpsPerCta = 36 * 4096;  // checkpoint capacity of one CTA
 constexpr double kStarveSeconds = 0.25;         // a queued request blocks later ones after this
 
 int64_t round_up(int64_t v, int64_t u) { return (v + u - 1) / u * u; }
@@ -573,7 +573,7 @@ sv_status sv_server_submit(sv_server* s, const sv_instance* inst, const double* 
   r.etraj.assign(n_steps, 0.0);
   if (r.small) {
     r.n_ckpt = segment_ops(r.hc.ops, 2, 3, r.segs);
-    if (((int64_t)r.n_ckpt << r.n) * class_teams(r.n) > kCkptAmpsPerCta) {
+    if (team_ckpt_amps(r.n_ckpt, r.n) * class_teams(r.n) > kCkptAmpsPerCta) {
       set_error("circuit needs %d checkpoints of 2^%d amplitudes, more than the server's "
                 "scratch holds", r.n_ckpt, r.n);
       return SV_EINVAL;
