@@ -844,7 +844,7 @@ __device__ void run_instance(const BatchArgs& a, int idx, const Team& T, TeamS& 
         constexpr int kHB = 4;
         constexpr int kHU = 16;
         const int nhb = n - T.log_size;
-        double W = 0.0, hb[kHB] = {0.0, 0.0, 0.0, 0.0};
+        double W = 0.0, hb[kHB] = {0.0, 0.0, 0.0, 0.0}, wq[4];
         double2 lr[kHU];
         // the thread's amplitudes are k = tid + u TS for u < nu (index bit log_size + q is
         // bit q of u)
@@ -858,10 +858,27 @@ __device__ void run_instance(const BatchArgs& a, int idx, const Team& T, TeamS& 
             const double2 pk = psi[src];
             double2 lk = lam[src];
             const double w = fma(lk.x, pk.y, dneg(lk.y) * pk.x);
-            W += w;
+            if (nu >= 4) {
+              // nu = 2^nhb >= 4: the sums over slots u are reduced four at a time, a partial
+              // butterfly (3 DADD per amplitude instead of 1 + nhb)
+              wq[u & 3] = w;
+              if ((u & 3) == 3) {
+                const double s01 = wq[0] + wq[1], d01 = wq[0] - wq[1];
+                const double s23 = wq[2] + wq[3], d23 = wq[2] - wq[3];
+                const double Sq = s01 + s23;
+                W += Sq;
+                hb[0] += d01 + d23;
+                hb[1] += s01 - s23;
 #pragma unroll
-            for (int q = 0; q < kHB; ++q)
-              if (q < nhb) hb[q] += ((u >> q) & 1) ? dneg(w) : w;
+                for (int q = 2; q < kHB; ++q)
+                  if (q < nhb) hb[q] += ((u >> q) & 1) ? dneg(Sq) : Sq;
+              }
+            } else {
+              W += w;
+#pragma unroll
+              for (int q = 0; q < kHB; ++q)
+                if (q < nhb) hb[q] += ((u >> q) & 1) ? dneg(w) : w;
+            }
             const double2 ph = cmul(S.th[k >> hl], S.tl[k & lmask]);
             lk = cmul_conj(lk, ph);
             if (ncz && cz_sign(S, ncz, k)) lk = make_double2(dneg(lk.x), dneg(lk.y));
