@@ -180,6 +180,22 @@ sv_status sv_ham_lower(const sv_paulisum* h, int32_t kmax, int32_t* n_groups, in
 sv_status sv_circuit_plan(const sv_circuit* circuit, int32_t tile_bits, int32_t* n_passes,
                           int32_t* pass_of_gate);
 
+/* Host-only inspection of the segments the batched kernel runs a circuit as (no device work):
+ * *n_segs receives their number and *n_ckpt the checkpoint slots they use.  If segs is not
+ * NULL it receives cap rows of 5 int32 (kind, split, first gate, gate count, checkpoint slot
+ * or -1), in forward order; cap smaller than the segment count is SV_EINVAL.  Kinds:
+ *   0 plain gates, applied one at a time;
+ *   1 RY (or RX) gates on distinct qubits (split 1: the first segment, all RY, acting on the
+ *     reference state, written as a product state);
+ *   2 a run of RZ and CZ gates with at least 3 RZ (at most 16 RZ and 16 CZ);
+ *   3 a run of 2 to 32 CNOT/X gates;
+ *   4 a kind-2 run directly followed by a kind-3 run (split = gates of the diagonal part).
+ * Each checkpoint slot holds a state; a kind-4 segment also keeps its tables there.
+ * *team_scratch_amps (if not NULL) receives the checkpoint scratch one instance needs, in
+ * amplitudes.  Gates are numbered as in the circuit. */
+sv_status sv_batch_segments(const sv_circuit* circuit, int32_t cap, int32_t* segs,
+                            int32_t* n_segs, int32_t* n_ckpt, int64_t* team_scratch_amps);
+
 /* ---------------------------------------------------------------- one state */
 
 /* psi = |basis_index> (Eq. 4); also records it as the context's reference state, the

@@ -362,6 +362,35 @@ sv_status sv_circuit_plan(const sv_circuit* circ, int32_t tile_bits, int32_t* n_
   return SV_OK;
 }
 
+sv_status sv_batch_segments(const sv_circuit* circ, int32_t cap, int32_t* segs_out,
+                            int32_t* n_segs, int32_t* n_ckpt, int64_t* team_scratch_amps) {
+  clear_error();
+  if (!n_segs || !n_ckpt) { set_error("NULL argument"); return SV_EINVAL; }
+  HostCircuit hc;
+  sv_status st = lower_circuit(circ, 0, hc);
+  if (st != SV_OK) return st;
+  std::vector<Seg> sg;
+  const int nc = segment_ops(hc.ops, 2, 3, sg);  // as sv_batch_create segments each circuit
+  *n_segs = (int32_t)sg.size();
+  *n_ckpt = nc;
+  if (team_scratch_amps) *team_scratch_amps = team_ckpt_amps(nc, hc.n);
+  if (segs_out) {
+    if (cap < (int32_t)sg.size()) {
+      set_error("%d segments, room for %d", (int)sg.size(), cap);
+      return SV_EINVAL;
+    }
+    for (size_t i = 0; i < sg.size(); ++i) {
+      int32_t* r = segs_out + 5 * i;
+      r[0] = sg[i].kind;
+      r[1] = sg[i].split;
+      r[2] = sg[i].first;
+      r[3] = sg[i].count;
+      r[4] = sg[i].ckpt;
+    }
+  }
+  return SV_OK;
+}
+
 // ------------------------------------------------------------------------------ one state
 sv_status sv_init_reference(sv_ctx* c, uint64_t b) {
   clear_error();

@@ -80,6 +80,7 @@ def lib():
         "sv_ham_info": ([P, P, P], i32),
         "sv_ham_lower": ([P, i32, P, P, P, P, P, P, P], i32),
         "sv_circuit_plan": ([P, i32, P, P], i32),
+        "sv_batch_segments": ([P, i32, P, P, P, P], i32),
         "sv_init_reference": ([P, u64], i32),
         "sv_apply_circuit": ([P, P, P], i32),
         "sv_expval_paulisum": ([P, P, P], i32),
@@ -198,6 +199,21 @@ def circuit_plan(circuit, tile_bits=0):
     pog = np.zeros(max(len(C.gates), 1), np.int32)
     _check(lib().sv_circuit_plan(C.ref(), int(tile_bits), ctypes.byref(npass), _ptr(pog)))
     return npass.value, pog[:len(C.gates)]
+
+
+def batch_segments(circuit):
+    """Host-only segmentation of a circuit for the batched kernel: (segments as an (S, 5) int32
+    array of kind, split, first gate, gate count, checkpoint slot; checkpoint slots; checkpoint
+    scratch of one instance in amplitudes)."""
+    C = circuit if isinstance(circuit, Circuit) else Circuit(circuit)
+    ns, nc = ctypes.c_int32(), ctypes.c_int32()
+    amps = ctypes.c_int64()
+    _check(lib().sv_batch_segments(C.ref(), 0, None, ctypes.byref(ns), ctypes.byref(nc),
+                                   ctypes.byref(amps)))
+    segs = np.zeros((max(ns.value, 1), 5), np.int32)
+    _check(lib().sv_batch_segments(C.ref(), ns.value, _ptr(segs), ctypes.byref(ns),
+                                   ctypes.byref(nc), None))
+    return segs[:ns.value], nc.value, amps.value
 
 
 GROUP_DTYPE = np.dtype([("x_mask", "<u8"), ("z_union", "<u8"), ("z_bits", "<i4"),
