@@ -28,6 +28,17 @@ def test_h2_sweep_batch():
     _check(b, insts, e, g)
 
 
+def test_h2_sto3g_sweep_batch():
+    """The real molecule (STO-3G, Jordan-Wigner) over the paper's 100 bond lengths."""
+    from paper_2601_09951_gb300 import h2_sto3g
+    insts = h2_sto3g.h2_sto3g_sweep(100)
+    for k, inst in enumerate(insts):
+        inst["theta"] = np.array([0.05 * k - 2.0])
+    b = svqe.Batch(insts)
+    e, g = b.run(b.theta_of(insts))
+    _check(b, insts, e, g)
+
+
 def test_hea_batch_small_sample():
     insts = W.hea_batch(48)
     b = svqe.Batch(insts)
