@@ -79,24 +79,29 @@ def test_context_options_reject_null_handles():
     assert L.sv_tile_bits(None, None) == svqe.SV_EINVAL
 
 
-def _apply_lowered(n, lowered, psi):
+def _group_f(n, lowered, g):
+    """f_g(k) for every k, from the lowered group record and table."""
     x, zu, cls, toff, table = lowered
+    ks = np.arange(1 << n, dtype=np.uint64)
+    if cls[g] >= 4:  # one term: coefficient times the parity sign of z & k
+        par = np.array([bin(int(k) & int(zu[g])).count("1") & 1 for k in ks])
+        return table[toff[g]] * (1 - 2 * par)
+    idx = np.zeros(1 << n, dtype=np.int64)
+    m, b = int(zu[g]), 0
+    while m:
+        pos = (m & -m).bit_length() - 1
+        idx |= (((ks >> np.uint64(pos)) & np.uint64(1)).astype(np.int64)) << b
+        b += 1
+        m &= m - 1
+    return table[toff[g] + idx]
+
+
+def _apply_lowered(n, lowered, psi):
+    x = lowered[0]
     out = np.zeros_like(psi)
     ks = np.arange(1 << n, dtype=np.uint64)
     for g in range(len(x)):
-        if cls[g] >= 4:  # one term: coefficient times the parity sign of z & k
-            par = np.array([bin(int(k) & int(zu[g])).count("1") & 1 for k in ks])
-            f = table[toff[g]] * (1 - 2 * par)
-        else:
-            idx = np.zeros(1 << n, dtype=np.int64)
-            m, b = int(zu[g]), 0
-            while m:
-                pos = (m & -m).bit_length() - 1
-                idx |= (((ks >> np.uint64(pos)) & np.uint64(1)).astype(np.int64)) << b
-                b += 1
-                m &= m - 1
-            f = table[toff[g] + idx]
-        out += f * psi[(ks ^ x[g]).astype(np.int64)]
+        out += _group_f(n, lowered, g) * psi[(ks ^ x[g]).astype(np.int64)]
     return out
 
 
@@ -127,6 +132,38 @@ def test_grouped_tables_reproduce_dense_h_psi(n, kmax):
             assert np.all(t.real == 0)
     if n >= 6:  # registers this wide leave most X masks with a single term
         assert any(c >= 4 for c in lowered[2]) and any(c < 4 for c in lowered[2])
+
+
+@pytest.mark.parametrize("n", [1, 4, 7])
+def test_lowered_groups_are_hermitian_and_pair_sums_give_the_energy(n):
+    """The energy-only kernel visits one member k of each pair (k, k ^ x_g), the one with the
+    top bit of x_g clear, and adds 2 Re(conj(psi_k) f_g(k) psi_{k ^ x_g}); the diagonal group
+    pairs k with k + N/2.  That needs f_g(k ^ x_g) = conj f_g(k) from the lowered tables.  The
+    same summation in NumPy must give psi^H H psi."""
+    rng = np.random.default_rng(700 + n)
+    ham = W.random_pauli_sum(rng, n, 80, 0.4, min(4, n), 1.0)
+    lowered = svqe.ham_lower(ham, n, 4)
+    x = lowered[0]
+    N = 1 << n
+    ks = np.arange(N, dtype=np.int64)
+    psi = rng.normal(size=N) + 1j * rng.normal(size=N)
+    e = 0.0
+    for g in range(len(x)):
+        f = _group_f(n, lowered, g)
+        xg = int(x[g])
+        xp = xg if xg else N >> 1
+        np.testing.assert_allclose(f[ks ^ xg], np.conj(f), rtol=1e-14, atol=1e-14)
+        h = xp.bit_length() - 1
+        lo = (1 << h) - 1
+        t = np.arange(N >> 1, dtype=np.int64)
+        k = ((t & ~lo) << 1) | (t & lo)
+        v, w = psi[k], psi[k ^ xp]
+        if xg == 0:
+            e += np.sum(f[k].real * np.abs(v) ** 2 + f[k ^ xp].real * np.abs(w) ** 2)
+        else:
+            e += 2.0 * np.sum((np.conj(v) * f[k] * w).real)
+    want = np.vdot(psi, D.ham_dense(n, ham) @ psi).real
+    assert abs(e - want) <= 1e-12 * max(1.0, abs(want))
 
 
 def test_lowering_rejects_bad_masks():
