@@ -125,3 +125,7 @@ def test_empty_circuit_and_small_capacity():
     st = svqe.lib().sv_batch_segments(C.ref(), 1, buf.ctypes.data, ctypes.byref(ns),
                                       ctypes.byref(nc), None)
     assert st == 1  # SV_EINVAL: more segments than rows
+    # NULL circuit or outputs: SV_EINVAL, nothing written
+    assert svqe.lib().sv_batch_segments(None, 0, None, ctypes.byref(ns), ctypes.byref(nc),
+                                        None) == 1
+    assert svqe.lib().sv_batch_segments(C.ref(), 0, None, None, None, None) == 1
