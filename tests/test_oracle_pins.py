@@ -330,6 +330,98 @@ def test_adam_first_step_and_scale_invariance():
     np.testing.assert_allclose(es10, 10 * es, rtol=1e-6, atol=1e-9)
 
 
+def _stub_gradients(monkeypatch, grads):
+    """Make oracle.energy_grad return grads[k] on its k-th call (energy = k), so that the
+    optimizer's own arithmetic is all that the trajectory shows."""
+    calls = []
+
+    def fake(inst, theta=None):
+        k = len(calls)
+        calls.append(np.array(theta, dtype=np.float64))
+        return float(k), np.array(grads[k], dtype=np.float64)
+
+    monkeypatch.setattr(oracle, "energy_grad", fake)
+    return calls
+
+
+def test_adam_constant_gradient_steps_by_lr_at_every_step(monkeypatch):
+    """With a constant gradient g, m_t = (1 - b1^t) g and v_t = (1 - b2^t) g^2, so the two
+    bias corrections give m_hat = g and v_hat = g^2 at every t (Kingma & Ba; the paper's
+    optimizer, Sec. 3.4) and every step is exactly -lr * g / (|g| + eps).  A bias correction
+    with a fixed exponent (1 - b^1 at every t) or a dropped one moves every step after the
+    first away from this value."""
+    g = np.array([0.3, -2.0, 1e-3, 7.5])
+    T, lr = 50, 0.01
+    inst = {"theta": np.array([0.1, -0.2, 0.3, 0.0])}
+    calls = _stub_gradients(monkeypatch, [g] * T)
+    es, ths, th_end = oracle.adam_trajectory(inst, lr, T)
+    assert len(calls) == T and np.array_equal(es, np.arange(T, dtype=float))
+    steps = np.diff(np.vstack([ths, th_end]), axis=0)
+    want = -lr * g / (np.abs(g) + 1e-8)
+    for t in range(T):
+        np.testing.assert_allclose(steps[t], want, rtol=1e-12, atol=0, err_msg=f"step {t + 1}")
+    for t in range(T):  # the gradient is evaluated at theta_t, before the update
+        assert np.array_equal(calls[t], ths[t])
+
+
+def test_adam_hand_computed_second_and_third_steps(monkeypatch):
+    """Steps 2 and 3 for gradients whose sign or size changes, worked by hand with
+    b1 = 0.9, b2 = 0.999 (per parameter, g0 = the first gradient):
+      signs +g0, -g0, +g0:
+        m1 = 0.1 g0;  m2 = 0.09 g0 - 0.1 g0 = -0.01 g0;  m3 = -0.009 g0 + 0.1 g0 = 0.091 g0
+        m_hat2 = -0.01/(1 - 0.81) g0 = -g0/19;  m_hat3 = 0.091/(1 - 0.729) g0 = 91/271 g0
+        v_t = (1 - 0.999^t) g0^2, so v_hat = g0^2 and step_t = -lr m_hat_t / (|g0| + eps);
+      sizes g0, 2 g0:
+        m2 = 0.09 g0 + 0.2 g0 = 0.29 g0, m_hat2 = 29/19 g0
+        v2 = 0.999 * 0.001 g0^2 + 0.001 * 4 g0^2 = 0.004999 g0^2,
+        v_hat2 = 0.004999 / (1 - 0.998001) g0^2 = 4999/1999 g0^2
+        step2 = -lr (29/19) g0 / (sqrt(4999/1999) |g0| + eps)."""
+    lr, eps = 0.01, 1e-8
+    g0 = np.array([0.5, -1.25, 3.0])
+    inst = {"theta": np.zeros(3)}
+    _stub_gradients(monkeypatch, [g0, -g0, g0])
+    _, ths, th_end = oracle.adam_trajectory(inst, lr, 3)
+    steps = np.diff(np.vstack([ths, th_end]), axis=0)
+    np.testing.assert_allclose(steps[1], -lr * (-1.0 / 19.0) * g0 / (np.abs(g0) + eps),
+                               rtol=1e-12)
+    np.testing.assert_allclose(steps[2], -lr * (91.0 / 271.0) * g0 / (np.abs(g0) + eps),
+                               rtol=1e-12)
+    _stub_gradients(monkeypatch, [g0, 2 * g0])
+    _, ths, th_end = oracle.adam_trajectory(inst, lr, 2)
+    steps = np.diff(np.vstack([ths, th_end]), axis=0)
+    want = -lr * (29.0 / 19.0) * g0 / (np.sqrt(4999.0 / 1999.0) * np.abs(g0) + eps)
+    np.testing.assert_allclose(steps[1], want, rtol=1e-12)
+
+
+def test_gd_trajectory_follows_the_h2_closed_form():
+    """Gradient descent on the one-parameter H2 ansatz (the configured bond-length loop:
+    step 0.4, 50 steps from theta = 0).  With E = a + b cos t + c sin t (hand-derived above),
+    every recorded step is (E(theta_t), E'(theta_t), theta_t) and theta_{t+1} =
+    theta_t - 0.4 (-b sin theta_t + c cos theta_t).  The iteration is checked one step at a
+    time from the oracle's own theta_t, so that the chaotic bonds (0.4 |E''| > 2) are pinned
+    as tightly as the contracting ones; where the map contracts, the whole closed-form
+    trajectory is followed as well."""
+    lr, T = 0.4, 50
+    for inst in W.h2_sweep(100)[::3]:
+        a, b, c = _h2_closed_form_abc(inst["ham"]["coeff"])
+        es, gs, ths, th_end = oracle.gd_trajectory(inst, lr, T, theta0=np.zeros(1))
+        assert es.shape == (T,) and gs.shape == (T, 1) and ths.shape == (T, 1)
+        assert ths[0, 0] == 0.0
+        nxt = np.concatenate([ths[1:, 0], th_end])
+        for t in range(T):
+            th = ths[t, 0]
+            assert abs(es[t] - (a + b * np.cos(th) + c * np.sin(th))) <= 1e-13
+            gc = -b * np.sin(th) + c * np.cos(th)
+            assert abs(gs[t, 0] - gc) <= 1e-13
+            assert abs(nxt[t] - (th - lr * gc)) <= 1e-13
+        R = np.hypot(b, c)
+        if abs(1 - lr * R) < 0.9:
+            th = 0.0
+            for t in range(T):
+                th = th - lr * (-b * np.sin(th) + c * np.cos(th))
+            assert abs(th - th_end[0]) <= 1e-9
+
+
 def test_tfim_workload_is_the_ising_chain_and_respects_the_variational_bound():
     """The scaling study's Hamiltonian generator gives -J sum Z_i Z_{i+1} - h sum X_i on an open
     chain (built here from Kronecker products), and the oracle's energy of its ansatz state
