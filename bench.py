@@ -260,8 +260,8 @@ def run_serve(args):
 HBM_PEAK_GBS = 6678.2  # measured copy bandwidth (read + write) of a GB300
 
 # dram__bytes_read.sum + dram__bytes_write.sum of one k_batch launch of the default workload,
-# from the ncu capture recorded in profiles/k_batch_hea_batch.md, keyed by a hash of the
-# kernel's sources: once the kernel changes the key no longer matches and traffic is null.
+# from one ncu capture of that launch, keyed by a hash of the kernel's sources: once the
+# kernel changes the key no longer matches and traffic is null.
 KBATCH_TRAFFIC = {"fa0046678f00f781": 373.54e6 + 519.86e6}
 KBATCH_SOURCES = ("k_batch.cu", "svqe_internal.cuh", "svqe_types.h", "launch.h")
 

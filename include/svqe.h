@@ -201,12 +201,18 @@ sv_status sv_batch_segments(const sv_circuit* circuit, int32_t cap, int32_t* seg
 /* psi = |basis_index> (Eq. 4); also records it as the context's reference state, the
  * starting point of sv_adjoint_grad and vqe_step.  basis_index must be < 2^n. */
 sv_status sv_init_reference(sv_ctx* ctx, uint64_t basis_index);
-/* psi <- U(theta) psi, gates in order.  theta: host array of circuit->n_params angles. */
+/* psi <- U(theta) psi, gates in list order (Sec. 3.3, Eq. 4-5: the ansatz acting on the
+ * reference state).  theta: host array of circuit->n_params angles; a gate whose param is -1
+ * uses its fixed_angle.  SV_EINVAL for a malformed gate record (unknown type, wire outside
+ * [0, n), duplicate wire, parameter index out of range) or circuit->n_qubits != the
+ * context's n; nothing is applied then. */
 sv_status sv_apply_circuit(sv_ctx* ctx, const sv_circuit* circuit, const double* theta);
 /* *energy_out = <psi|H|psi> for the context's current psi (Eq. 2). */
 sv_status sv_expval_paulisum(sv_ctx* ctx, const sv_ham* h, double* energy_out);
-/* Energy and gradient of E(theta) = <ref|U^dag H U|ref>, with |ref> the reference state of the
- * last sv_init_reference (|0> if none).  Forward pass, lambda = H psi, then the adjoint sweep
+/* Energy and gradient of E(theta) = <ref|U^dag H U|ref> (Sec. 3.1, Eq. 2 with the state of
+ * Eq. 4; the gradient step of Algorithm 1, Sec. 4.3), with |ref> the reference state of the
+ * last sv_init_reference (|0> if none).  The paper differentiates by parameter shift; this
+ * call reaches the same gradient by the adjoint method.  Forward pass, lambda = H psi, then the adjoint sweep
  * over gates in reverse: g_p += 2 Im<lambda|G_l|psi> for each gate l with parameter p, then
  * psi <- U_l^dag psi and lambda <- U_l^dag lambda.  Uses psi and lambda only, unless
  * checkpoints are enabled (sv_set_checkpoint_bytes).  energy_out:
@@ -356,15 +362,23 @@ sv_status sv_server_destroy(sv_server* s);
  * states of at most SV_NOALLOC_MAX_QUBITS qubits and circuits of at most
  * SV_NOALLOC_MAX_GATES gates; larger requests are rejected with SV_EINVAL and a message
  * naming the limit.
- *   circuit     host gate records (validated as for sv_apply_circuit).
- *   ref         basis index of the reference state, < 2^n.
- *   groups_dev  device array of n_groups sv_group records and tables_dev the device array of
- *               interleaved complex128 table entries, both as sv_ham_lower reports them for
- *               the Hamiltonian (x_mask, z_union, z_bits = popcount(z_union), cls,
- *               table_offset).
- *   theta_dev   device array of circuit->n_params angles.
- *   energy_dev  device address receiving E; grad_dev device array of n_params derivatives.
- *   cuda_stream cudaStream_t to order the work on (NULL: the legacy default stream).
+ *   circuit      host gate records (validated as for sv_apply_circuit).
+ *   ref          basis index of the reference state, < 2^n.
+ *   ham_n_qubits the register width the group records were lowered for; it must equal
+ *                circuit->n_qubits (SV_EINVAL otherwise), because a wire maps to bit n-1-wire
+ *                and records lowered for another width describe another operator.
+ *   groups_dev   device array (8-byte aligned) of n_groups sv_group records, and tables_dev
+ *                the device array of n_table interleaved complex128 table entries, both as
+ *                sv_ham_lower reports them for the Hamiltonian (x_mask, z_union,
+ *                z_bits = popcount(z_union), cls, table_offset).  n_groups <= 2^n.
+ *   theta_dev    device array of circuit->n_params angles.
+ *   energy_dev   device address receiving E; grad_dev device array of n_params derivatives.
+ *   cuda_stream  cudaStream_t to order the work on (NULL: the legacy default stream).
+ * The records sit in device memory, so the host cannot read them: a kernel checks each one
+ * (masks inside the register, a known class, its table range inside [0, n_table)) before
+ * anything is read through it.  If any record fails, no out-of-range read happens and the
+ * call writes NaN to energy_dev and grad_dev; the status is still SV_OK, since the call
+ * returns before the check runs.
  * Stream-ordered; returns without synchronising.  The first call on a device looks up the
  * array's device address once (cudaGetSymbolAddress with that device current); make that
  * first call before any stream capture.  Every call on a device shares the one array and
@@ -380,12 +394,13 @@ typedef struct {
 
 #define SV_NOALLOC_MAX_QUBITS 14
 #define SV_NOALLOC_MAX_GATES 256
-#define SV_NOALLOC_SCRATCH_BYTES (3u << 20)
+#define SV_NOALLOC_SCRATCH_BYTES (4u << 20)
 
 sv_status sv_adjoint_grad_noalloc(const sv_circuit* circuit, uint64_t ref,
-                                  const sv_group* groups_dev, int32_t n_groups,
-                                  const double* tables_dev, const double* theta_dev,
-                                  double* energy_dev, double* grad_dev, void* cuda_stream);
+                                  int32_t ham_n_qubits, const sv_group* groups_dev,
+                                  int32_t n_groups, const double* tables_dev, int64_t n_table,
+                                  const double* theta_dev, double* energy_dev,
+                                  double* grad_dev, void* cuda_stream);
 
 #ifdef __cplusplus
 }

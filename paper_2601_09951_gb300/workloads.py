@@ -16,8 +16,8 @@ x = bits where the factor is X or Y, z = bits where it is Z or Y.
 
 Shapes follow the paper's workloads (Sec. 2.2: 100 bond lengths on [0.1, 3.0] A; Sec. 3.3: HF
 reference and one DoubleExcitation on 4 qubits; Sec. 3.2: a Jordan-Wigner Pauli sum; Sec. 5.2:
-a qubit-count scaling study).  The coefficients are synthetic: the real H2/STO-3G integrals
-are not part of this project.
+a qubit-count scaling study).  The coefficients here are synthetic; the real H2/STO-3G
+Hamiltonian over the same bond lengths comes from ``h2_sto3g.py``.
 """
 import itertools
 import math
