@@ -98,7 +98,7 @@ def lib():
         "sv_batch_run_dev": ([P, P, P, P], i32),
         "sv_batch_vqe_dev": ([P, P, dbl, i32, P], i32),
         "sv_batch_adam_dev": ([P, P, dbl, i32, P, i32], i32),
-        "sv_adjoint_grad_noalloc": ([P, u64, P, i32, P, P, P, P, P], i32),
+        "sv_adjoint_grad_noalloc": ([P, u64, i32, P, i32, P, i64, P, P, P, P], i32),
         "sv_server_create": ([P, P], i32),
         "sv_server_submit": ([P, P, P, i32, dbl, P], i32),
         "sv_server_wait": ([P, u64, i32, P, P, P], i32),
@@ -233,15 +233,18 @@ def group_records(ham, n, kmax=14):
     return rec, np.ascontiguousarray(table, dtype=np.complex128)
 
 
-def adjoint_grad_noalloc(circuit, ref, groups_ptr, n_groups, tables_ptr, theta_ptr, energy_ptr,
-                         grad_ptr, stream=None):
+def adjoint_grad_noalloc(circuit, ref, ham_n_qubits, groups_ptr, n_groups, tables_ptr,
+                         n_table, theta_ptr, energy_ptr, grad_ptr, stream):
     """sv_adjoint_grad_noalloc: every pointer is a device address the caller owns; the
-    library allocates no device memory.  Stream-ordered (synchronise before reading)."""
+    library allocates no device memory.  `stream` is the integer handle of the CUDA stream the
+    inputs were written on (for torch: torch.cuda.current_stream().cuda_stream); unlike the
+    context calls there is no library-owned stream here, and 0 means torch's default stream.
+    Stream-ordered (synchronise before reading)."""
     C = circuit if isinstance(circuit, Circuit) else Circuit(circuit)
     _check(lib().sv_adjoint_grad_noalloc(
-        C.ref(), int(ref), ctypes.c_void_p(groups_ptr), int(n_groups),
-        ctypes.c_void_p(tables_ptr), ctypes.c_void_p(theta_ptr), ctypes.c_void_p(energy_ptr),
-        ctypes.c_void_p(grad_ptr), _stream_arg(stream)))
+        C.ref(), int(ref), int(ham_n_qubits), ctypes.c_void_p(groups_ptr), int(n_groups),
+        ctypes.c_void_p(tables_ptr), int(n_table), ctypes.c_void_p(theta_ptr),
+        ctypes.c_void_p(energy_ptr), ctypes.c_void_p(grad_ptr), _stream_arg(int(stream))))
 
 
 class Ham:
