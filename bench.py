@@ -40,7 +40,8 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", default="batch",
-                    choices=["batch", "serve", "kernels", "single", "h2", "classes", "tfim"],
+                    choices=["batch", "serve", "kernels", "single", "h2", "classes", "tfim",
+                             "fp64"],
                     help="batch: the batched evaluation step (default); serve: the request "
                          "loop (latency percentiles), printed as its own JSON line")
     ap.add_argument("--requests", type=int, default=300)
@@ -54,6 +55,9 @@ def parse():
                     help="single: autotune the fused tile size first (sv_set_autotune)")
     ap.add_argument("--per-circuit-sample", type=int, default=512,
                     help="batch: instances timed through the one-circuit-per-launch path")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="batch: skip the FP64 probe, the 26-qubit kernel table and the "
+                         "serving sample that the default line carries")
     return ap.parse_args()
 
 
@@ -145,24 +149,34 @@ class ClockSampler:
                 "power_w_max": max(float(r[4]) for r in rows if r[4].strip()[0].isdigit())}
 
 
-def cpu_baseline(args, seconds, first_index=0):
-    """The oracle (parameter-shift gradient, OpenMP over shifted evaluations on all host
-    cores) on consecutive instances of the same seeded workload until `seconds` elapse."""
+def cpu_baseline(args, seconds, first_index=0, one_core_seconds=5.0):
+    """The oracle (parameter-shift gradient, OpenMP over shifted evaluations) on consecutive
+    instances of the same seeded workload: on all host cores until `seconds` elapse, then on
+    one core for `one_core_seconds`."""
     import oracle
     from paper_2601_09951_gb300 import workloads as W
     cores = os.cpu_count() or 1
+
+    def timed(threads, budget, start):
+        oracle.set_threads(threads)
+        done, t0, i = 0, time.perf_counter(), start
+        while time.perf_counter() - t0 < budget:
+            inst = W.hea_batch(args.instances, seed=args.seed, indices=[i % args.instances])[0]
+            oracle.energy_grad(inst)
+            done += 1
+            i += 1
+        return done, time.perf_counter() - t0, i
+
+    done, dt, i = timed(cores, seconds, first_index)
+    used = oracle.get_threads()
+    done1, dt1, i1 = timed(1, one_core_seconds, first_index)
     oracle.set_threads(cores)
-    done, t0 = 0, time.perf_counter()
-    i = first_index
-    while time.perf_counter() - t0 < seconds:
-        inst = W.hea_batch(args.instances, seed=args.seed, indices=[i % args.instances])[0]
-        oracle.energy_grad(inst)
-        done += 1
-        i += 1
-    dt = time.perf_counter() - t0
-    return {"value": done / dt, "unit": UNIT, "cores": oracle.get_threads(), "kind": "oracle",
+    return {"value": done / dt, "unit": UNIT, "cores": used, "kind": "oracle",
             "sample": f"instances {first_index}..{i - 1} of the same seeded workload "
-                      f"({done} energy+gradient evaluations, parameter-shift, {dt:.1f} s)"}
+                      f"({done} energy+gradient evaluations, parameter-shift, {dt:.1f} s)",
+            "one_core": {"value": done1 / dt1, "unit": UNIT, "cores": 1,
+                         "sample": f"instances {first_index}..{i1 - 1}, {done1} evaluations, "
+                                   f"{dt1:.1f} s"}}
 
 
 def run_reference(args):
@@ -199,12 +213,45 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def serve_run(svqe, reqs, rate, serial=False, budget=64 << 30):
+    """One pass of a request stream through the server: arrivals scaled to `rate` requests/s
+    (None: all at once), p50/p99 latency from submit to completion, evals/s over the wall
+    time."""
+    import threading
+    srv = svqe.Server(hbm_budget_bytes=budget, steps_per_tick=2, serial=serial)
+    ids = [None] * len(reqs)
+    t0 = time.perf_counter()
+
+    def submitter():
+        for k, r in enumerate(reqs):
+            if rate:
+                # arrival_s in the stream is for 1 request/s; scale it to `rate`
+                delay = r["arrival_s"] / rate - (time.perf_counter() - t0)
+                if delay > 0:
+                    time.sleep(delay)
+            ids[k] = srv.submit(r, r["steps"], r["lr"])
+
+    th = threading.Thread(target=submitter)
+    th.start()
+    th.join()
+    lat = []
+    for rid in ids:
+        _, _, info = srv.wait(rid, -1)
+        lat.append(info.done_s - info.submit_s)
+    wall = time.perf_counter() - t0
+    st = srv.stats()
+    srv.close()
+    evals = sum(r["steps"] for r in reqs)
+    return {"evals_per_s": evals / wall, "p50_ms": 1e3 * float(np.percentile(lat, 50)),
+            "p99_ms": 1e3 * float(np.percentile(lat, 99)), "wall_s": wall,
+            "launches": int(st.launches), "peak_bytes": int(st.peak_bytes_in_use)}
+
+
 def run_serve(args):
     """Serving stream: Poisson arrivals of VQE requests (n log-uniform in 4..24, 20 gradient
     steps each).  Saturated throughput first (all requests at once), then arrivals at 25, 50,
     75 and 90 % of it with p50/p99 latency, beside the same stream through the serial
-    one-request-at-a-time server."""
-    import threading
+    one-request-at-a-time server at the same rates."""
     import torch
     torch.cuda.set_device(0)
     from paper_2601_09951_gb300 import build as libbuild
@@ -212,49 +259,35 @@ def run_serve(args):
     from paper_2601_09951_gb300 import svqe
     from paper_2601_09951_gb300 import workloads as W
     reqs = W.serve_stream(args.requests, 1.0, seed=1005)
-
-    def run(rate, serial=False, budget=64 << 30):
-        srv = svqe.Server(hbm_budget_bytes=budget, steps_per_tick=2, serial=serial)
-        ids = [None] * len(reqs)
-        t0 = time.perf_counter()
-
-        def submitter():
-            for k, r in enumerate(reqs):
-                if rate:
-                    delay = r["arrival_s"] / rate * 1.0 - (time.perf_counter() - t0)
-                    if delay > 0:
-                        time.sleep(delay)
-                ids[k] = srv.submit(r, r["steps"], r["lr"])
-
-        th = threading.Thread(target=submitter)
-        th.start()
-        th.join()
-        lat = []
-        for rid in ids:
-            _, _, info = srv.wait(rid, -1)
-            lat.append(info.done_s - info.submit_s)
-        wall = time.perf_counter() - t0
-        st = srv.stats()
-        srv.close()
-        evals = sum(r["steps"] for r in reqs)
-        return {"evals_per_s": evals / wall, "p50_ms": 1e3 * float(np.percentile(lat, 50)),
-                "p99_ms": 1e3 * float(np.percentile(lat, 99)), "wall_s": wall,
-                "launches": int(st.launches), "peak_bytes": int(st.peak_bytes_in_use)}
-
-    sat = run(None)
+    sat = serve_run(svqe, reqs, None)
     req_rate = args.requests / sat["wall_s"]  # requests/s at saturation
-    sweep = {}
+    sweep, serial = {}, {}
     for frac in (0.25, 0.5, 0.75, 0.9):
-        # arrival_s in the stream is for 1 request/s; scale to frac of saturation
-        sweep[f"{int(frac * 100)}%"] = run(frac * req_rate)
-    serial_sat = run(None, serial=True)
-    serial_at_50 = run(0.5 * req_rate, serial=True)
+        sweep[f"{int(frac * 100)}%"] = serve_run(svqe, reqs, frac * req_rate)
+        serial[f"{int(frac * 100)}%"] = serve_run(svqe, reqs, frac * req_rate, serial=True)
+    serial_sat = serve_run(svqe, reqs, None, serial=True)
     line = {"metric": "serving: VQE energy+grad evals/s and p50/p99 request latency",
             "workload": f"serve_stream_{args.requests}_n4-24_20steps", "unit": "evals/s",
             "value": sat["evals_per_s"], "saturated": sat, "poisson": sweep,
-            "serial_saturated": serial_sat, "serial_at_50%": serial_at_50,
+            "serial_saturated": serial_sat, "serial_poisson": serial,
+            "batched_over_serial_saturated": sat["evals_per_s"] / serial_sat["evals_per_s"],
             "data": "synthetic (seeded Poisson stream)", "dtype": "f64"}
     print(json.dumps(line), flush=True)
+
+
+def serve_sample(svqe, W, n_requests=60):
+    """The serving loop on a short seeded stream, for the default line: saturated throughput,
+    then Poisson arrivals at 50 % of it (p50/p99), and the serial server saturated."""
+    reqs = W.serve_stream(n_requests, 1.0, seed=1005)
+    sat = serve_run(svqe, reqs, None)
+    half = serve_run(svqe, reqs, 0.5 * n_requests / sat["wall_s"])
+    serial = serve_run(svqe, reqs, None, serial=True)
+    return {"workload": f"serve_stream_{n_requests}_n4-24_20steps",
+            "saturated_evals_per_s": sat["evals_per_s"],
+            "at_50%": {"evals_per_s": half["evals_per_s"], "p50_ms": half["p50_ms"],
+                       "p99_ms": half["p99_ms"]},
+            "serial_saturated_evals_per_s": serial["evals_per_s"],
+            "batched_over_serial": sat["evals_per_s"] / serial["evals_per_s"]}
 
 
 HBM_PEAK_GBS = 6678.2  # measured copy bandwidth (read + write) of a GB300
@@ -298,17 +331,11 @@ def expval_flops_per_amp(ham):
     return total
 
 
-def run_kernels(args):
+def kernel_table(svqe, W, torch, n, subset=None):
     """Per-kernel timing on the single-state path at n qubits (state larger than L2): each
     kernel type through the public API, CUDA events on the context's stream, algorithmic bytes
-    and FP64 flops per amplitude, as listed beside each kernel below."""
-    import torch
-    torch.cuda.set_device(0)
-    from paper_2601_09951_gb300 import build as libbuild
-    libbuild.build()
-    from paper_2601_09951_gb300 import svqe
-    from paper_2601_09951_gb300 import workloads as W
-    n = args.qubits
+    and FP64 flops per amplitude, as listed beside each kernel below.  `subset`: names to run
+    (None: all)."""
     N = 1 << n
     stream = torch.cuda.Stream()
     ctx = svqe.Context(n, stream=stream.cuda_stream)
@@ -322,6 +349,8 @@ def run_kernels(args):
     rows = {}
 
     def timed(name, fn, bytes_per_amp, flops_per_amp, reps=5):
+        if subset is not None and not any(name.startswith(k) for k in subset):
+            return
         for _ in range(2):
             fn()
         torch.cuda.synchronize()
@@ -379,9 +408,92 @@ def run_kernels(args):
     timed("adjoint energy+gradient, 1 HEA layer (a8+a9)",
           lambda: ctx.adjoint_grad_dev(c1, th_d.data_ptr(), H, e_d.data_ptr(), g_d.data_ptr()),
           0, 0, reps=3)
+    H.close()
+    ctx.close()
+    return rows, peak, src
+
+
+def run_kernels(args):
+    import torch
+    torch.cuda.set_device(0)
+    from paper_2601_09951_gb300 import build as libbuild
+    libbuild.build()
+    from paper_2601_09951_gb300 import svqe
+    from paper_2601_09951_gb300 import workloads as W
+    n = args.qubits
+    rows, peak, src = kernel_table(svqe, W, torch, n)
     print(json.dumps({"metric": "single-state kernel throughput", "n_qubits": n,
-                      "state_bytes": 16 * N, "hbm_peak_GBps": peak, "hbm_peak_source": src,
-                      "fp64_peak_TFLOPs": FP64_PEAK_TFLOPS, "kernels": rows}), flush=True)
+                      "state_bytes": 16 * (1 << n), "hbm_peak_GBps": peak,
+                      "hbm_peak_source": src, "fp64_peak_TFLOPs": FP64_PEAK_TFLOPS,
+                      "kernels": rows}), flush=True)
+
+
+PROBE_SHAPES = [(bps, thr, ch) for bps in (1, 2, 4, 8) for thr in (128, 256)
+                for ch in (4, 8, 16)]
+
+
+def fp64_rate(svqe, torch, seconds=1.0, shapes=None):
+    """Measured FP64 FMA rate of the whole GPU (sv_fp64_probe).  Each shape (blocks per SM,
+    threads per block, independent FMA chains per thread) is timed over short launches with
+    CUDA events on the probe's stream; the fastest shape is then timed for about `seconds`
+    with SM clocks sampled meanwhile.  Returns the rate in FMA/s and FP64 TFLOP/s (FMA = 2
+    flops), per SM per clock at the median sampled clock, and every shape's rate."""
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    stream = torch.cuda.Stream()
+    out = torch.empty(8 * sms * 256, dtype=torch.float64, device="cuda")
+
+    def launch(shape, iters):
+        bps, thr, ch = shape
+        return svqe.fp64_probe(bps * sms, thr, ch, iters, out.data_ptr(), stream.cuda_stream)
+
+    def rate_of(shape, iters, reps):
+        ev = []
+        n_fma = 0.0
+        for _ in range(reps):
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            n_fma = launch(shape, iters)
+            b.record(stream)
+            ev.append((a, b))
+        torch.cuda.synchronize()
+        ms = sorted(a.elapsed_time(b) for a, b in ev)
+        return n_fma / (ms[len(ms) // 2] / 1e3), ms[len(ms) // 2]
+
+    with torch.cuda.stream(stream):
+        launch((1, 128, 4), 100)
+        torch.cuda.synchronize()
+        sweep = {}
+        for shape in (shapes or PROBE_SHAPES):
+            # about 20 ms per launch at 1e12 flop/s
+            iters = max(100, int(1e10 / (shape[0] * sms * shape[1] * shape[2])))
+            sweep[shape] = rate_of(shape, iters, 3)[0]
+        best = max(sweep, key=sweep.get)
+        iters = max(100, int(5e10 / (best[0] * sms * best[1] * best[2])))
+        with ClockSampler() as clk:
+            reps = max(3, int(seconds / 0.1))
+            rate, med = rate_of(best, iters, reps)
+        ck = clk.summary()
+    mhz = ck.get("sm_mhz") or 0.0
+    return {"fma_per_s": rate, "tflops": 2 * rate / 1e12,
+            "fma_per_clk_per_sm": rate / (mhz * 1e6) / sms if mhz else None,
+            "ms_per_launch_median": med, "sms": sms,
+            "shape": f"{best[0]} blocks/SM x {best[1]} threads x {best[2]} chains x {iters} FMA",
+            "sweep_tflops": {f"{b}x{t}x{c}": 2 * r / 1e12 for (b, t, c), r in sweep.items()},
+            "clocks": ck}
+
+
+def run_fp64(args):
+    import torch
+    torch.cuda.set_device(0)
+    from paper_2601_09951_gb300 import build as libbuild
+    libbuild.build()
+    from paper_2601_09951_gb300 import svqe
+    r = fp64_rate(svqe, torch, seconds=2.0)
+    r.update({"metric": "FP64 FMA issue rate (sv_fp64_probe)", "unit": "TFLOP/s",
+              "value": r["tflops"], "derived_peak_tflops": FP64_PEAK_TFLOPS,
+              "derived_peak_what": "2 FMA/clk/SM x 2 flop x 152 SMs x 2.07 GHz"})
+    print(json.dumps(r), flush=True)
 
 
 def run_single(args):
@@ -659,7 +771,8 @@ def main():
     if args.workload != "batch":
         if rank == 0:
             {"serve": run_serve, "kernels": run_kernels, "single": run_single,
-             "h2": run_h2, "classes": run_classes, "tfim": run_tfim}[args.workload](args)
+             "h2": run_h2, "classes": run_classes, "tfim": run_tfim,
+             "fp64": run_fp64}[args.workload](args)
         return
     import torch
     torch.cuda.set_device(local)
@@ -764,6 +877,24 @@ def main():
         pc = per_circuit(insts, args.per_circuit_sample)
         pc["batched_over_per_circuit"] = value / pc["value"]
         line["per_circuit"] = pc
+    if world == 1 and not args.no_extras:
+        # the measured FP64 rate beside the derived peak
+        probe = fp64_rate(svqe, torch, seconds=1.0)
+        line["roofline"]["peak_probe"] = probe["tflops"]
+        line["roofline"]["frac_of_probe"] = achieved / probe["tflops"]
+        line["fp64_probe"] = {k: probe[k] for k in ("tflops", "fma_per_clk_per_sm", "shape",
+                                                    "ms_per_launch_median")}
+        line["fp64_probe"]["sm_mhz"] = probe["clocks"].get("sm_mhz")
+        # the other two parts of the metric: HBM GB/s per kernel and serving latency
+        batch.close()
+        torch.cuda.empty_cache()
+        rows, peak, src = kernel_table(svqe, W, torch, 26,
+                                       subset=("RY mid", "CNOT", "expval"))
+        line["kernels_26q"] = {k: {"ms": v["ms"], "GB/s": v["GB/s"], "hbm_frac": v["hbm_frac"]}
+                               for k, v in rows.items()}
+        line["kernels_26q"]["hbm_peak_GBps"] = peak
+        torch.cuda.empty_cache()
+        line["serve"] = serve_sample(svqe, W)
     if world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(args, args.cpu_seconds)
     print(json.dumps(line), flush=True)

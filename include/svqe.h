@@ -296,9 +296,13 @@ sv_status sv_batch_adam_dev(sv_batch* b, double* theta_dev, double lr, int32_t n
  * (Algorithm 1's loop with a fixed step) and returns its final theta and the energies before
  * each update.  A request's results do not depend on which other requests shared its launches.
  * serial = 1 runs one request at a time, with no batching (the one-circuit-at-a-time baseline).
- * Zero fields take defaults: 4 GiB, 4096, 1, 4.  The server reserves a device arena of
- * min(hbm_budget_bytes, 6 GiB) for small requests at creation; large requests allocate their
- * own buffers when admitted.  The admitted requests' footprints never sum above the budget. */
+ * Zero fields take defaults: 4 GiB, 4096, 1, 8.  The server reserves a device arena of
+ * min(hbm_budget_bytes, 6 GiB) for small requests at creation; a large request gets its own
+ * buffers when admitted, and keeps them idle after it finishes for the next request of the same
+ * qubit count (at most max_active_large idle sets), so that steady-state admission and
+ * completion allocate and free nothing on the device.  The admitted requests' footprints and
+ * the idle buffers together never exceed the budget; idle buffers are freed when an admission
+ * needs their room. */
 typedef struct {
   uint64_t hbm_budget_bytes;
   int32_t max_active_small;
@@ -345,6 +349,20 @@ sv_status sv_server_cancel(sv_server* s, uint64_t id);
 sv_status sv_server_get_stats(sv_server* s, sv_server_stats* out);
 /* Cancel queued requests, finish running ones, free everything. */
 sv_status sv_server_destroy(sv_server* s);
+
+/* ---------------------------------------------------------------- measurement */
+
+/* FP64 issue-rate probe, the denominator of the batched kernel's roofline (that kernel is
+ * bound by double-precision arithmetic, not by memory).  It has no counterpart in the paper.
+ * Launches `blocks` x `threads` threads, each running `chains` (1, 2, 4, 8 or 16)
+ * independent chains of `iters` fused multiply-adds on doubles, on cuda_stream (NULL: the
+ * legacy default stream), and writes one double per thread to out_dev (device,
+ * blocks * threads doubles, caller-owned).  *dfma_out (host, may be NULL) receives the number
+ * of FMAs the launch executes.  The caller times the launch (for example with events on the
+ * same stream).  SV_EINVAL for threads not a multiple of 32 in [32, 1024], blocks < 1,
+ * iters < 1, another chain count or a NULL out_dev. */
+sv_status sv_fp64_probe(int32_t blocks, int32_t threads, int32_t chains, int32_t iters,
+                        double* out_dev, void* cuda_stream, double* dfma_out);
 
 /* ---------------------------------------------------------------- no device allocation */
 

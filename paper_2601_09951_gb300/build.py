@@ -15,7 +15,7 @@ OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "libsvqe.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 SOURCES = ["api.cu", "k_state.cu", "k_batch.cu", "k_fused.cu", "k_dp.cu", "noalloc.cu", "serve.cu",
-           "host_compile.cpp"]
+           "k_probe.cu", "host_compile.cpp"]
 
 
 def _nvcc():

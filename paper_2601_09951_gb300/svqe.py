@@ -99,6 +99,7 @@ def lib():
         "sv_batch_vqe_dev": ([P, P, dbl, i32, P], i32),
         "sv_batch_adam_dev": ([P, P, dbl, i32, P, i32], i32),
         "sv_adjoint_grad_noalloc": ([P, u64, i32, P, i32, P, i64, P, P, P, P], i32),
+        "sv_fp64_probe": ([i32, i32, i32, i32, P, P, P], i32),
         "sv_server_create": ([P, P], i32),
         "sv_server_submit": ([P, P, P, i32, dbl, P], i32),
         "sv_server_wait": ([P, u64, i32, P, P, P], i32),
@@ -245,6 +246,16 @@ def adjoint_grad_noalloc(circuit, ref, ham_n_qubits, groups_ptr, n_groups, table
         C.ref(), int(ref), int(ham_n_qubits), ctypes.c_void_p(groups_ptr), int(n_groups),
         ctypes.c_void_p(tables_ptr), int(n_table), ctypes.c_void_p(theta_ptr),
         ctypes.c_void_p(energy_ptr), ctypes.c_void_p(grad_ptr), _stream_arg(int(stream))))
+
+
+def fp64_probe(blocks, threads, chains, iters, out_ptr, stream):
+    """sv_fp64_probe: enqueue the FP64 FMA-rate probe on `stream` (integer handle, 0 = torch's
+    default stream); returns the number of FMAs the launch executes."""
+    d = ctypes.c_double()
+    _check(lib().sv_fp64_probe(int(blocks), int(threads), int(chains), int(iters),
+                               ctypes.c_void_p(out_ptr), _stream_arg(int(stream)),
+                               ctypes.byref(d)))
+    return d.value
 
 
 class Ham:
