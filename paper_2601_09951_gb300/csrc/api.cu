@@ -78,6 +78,7 @@ struct sv_ham {
   int n_groups = 0;
   DGroup* groups = nullptr;
   double2* tables = nullptr;
+  size_t groups_cap = 0, tables_cap = 0;  // allocated records / table entries
   uint64_t bytes = 0;
   double l1 = 0.0;
 };
@@ -250,31 +251,26 @@ sv_status sv_destroy(sv_ctx* c) {
 // ------------------------------------------------------------------------------ Hamiltonians
 static constexpr int kTableBitsState = 14;  // largest per-group table, single-state path
 
-sv_status sv_ham_upload(sv_ctx* c, const sv_paulisum* h, sv_ham** out) {
-  clear_error();
-  if (!c || !out) { set_error("NULL argument"); return SV_EINVAL; }
-  *out = nullptr;
-  SV_CHECK_STICKY(c);
+// Lower h for the context's register and copy it into H's device buffers, growing them only
+// when the new Pauli sum needs more room than they have.
+static sv_status ham_fill(sv_ctx* c, sv_ham* H, const sv_paulisum* h) {
   HostHam hh;
   sv_status st = lower_ham(h, c->n, kTableBitsState, hh);
   if (st != SV_OK) return st;
-  sv_ham* H = new (std::nothrow) sv_ham();
-  if (!H) { set_error("host allocation failed"); return SV_ENOMEM; }
+  const size_t ng = std::max<size_t>(1, hh.groups.size());
+  const size_t nt = std::max<size_t>(1, hh.tables.size());
+  if (grow(H->groups, H->groups_cap, ng) != cudaSuccess ||
+      grow(H->tables, H->tables_cap, nt) != cudaSuccess) {
+    cudaGetLastError();
+    set_error("device allocation of %llu bytes for a Hamiltonian failed",
+              (unsigned long long)(ng * sizeof(DGroup) + nt * sizeof(double2)));
+    return SV_ENOMEM;
+  }
   H->n = c->n;
   H->device = c->device;
   H->n_groups = (int)hh.groups.size();
   H->l1 = hh.l1;
-  const size_t gb = std::max<size_t>(1, hh.groups.size()) * sizeof(DGroup);
-  const size_t tb = std::max<size_t>(1, hh.tables.size()) * sizeof(double2);
-  H->bytes = gb + tb;
-  if (cudaMalloc((void**)&H->groups, gb) != cudaSuccess ||
-      cudaMalloc((void**)&H->tables, tb) != cudaSuccess) {
-    cudaGetLastError();
-    sv_ham_free(H);
-    set_error("device allocation of %llu bytes for a Hamiltonian failed",
-              (unsigned long long)(gb + tb));
-    return SV_ENOMEM;
-  }
+  H->bytes = H->groups_cap * sizeof(DGroup) + H->tables_cap * sizeof(double2);
   if (!hh.groups.empty())
     SV_CUDA(cudaMemcpyAsync(H->groups, hh.groups.data(), hh.groups.size() * sizeof(DGroup),
                             cudaMemcpyHostToDevice, c->stream), c);
@@ -282,9 +278,36 @@ sv_status sv_ham_upload(sv_ctx* c, const sv_paulisum* h, sv_ham** out) {
     SV_CUDA(cudaMemcpyAsync(H->tables, hh.tables.data(), hh.tables.size() * sizeof(double2),
                             cudaMemcpyHostToDevice, c->stream), c);
   SV_CUDA(cudaStreamSynchronize(c->stream), c);
+  return SV_OK;
+}
+
+sv_status sv_ham_upload(sv_ctx* c, const sv_paulisum* h, sv_ham** out) {
+  clear_error();
+  if (!c || !out) { set_error("NULL argument"); return SV_EINVAL; }
+  *out = nullptr;
+  SV_CHECK_STICKY(c);
+  sv_ham* H = new (std::nothrow) sv_ham();
+  if (!H) { set_error("host allocation failed"); return SV_ENOMEM; }
+  H->device = c->device;
+  const sv_status st = ham_fill(c, H, h);
+  if (st != SV_OK) {
+    sv_ham_free(H);
+    return st;
+  }
   *out = H;
   return SV_OK;
 }
+
+namespace svqe {
+sv_status ham_reload(sv_ctx* c, sv_ham* H, const sv_paulisum* h) {
+  clear_error();
+  if (!c || !H) { set_error("NULL argument"); return SV_EINVAL; }
+  SV_CHECK_STICKY(c);
+  if (H->device != c->device) { set_error("Hamiltonian on another device"); return SV_EINVAL; }
+  return ham_fill(c, H, h);
+}
+bool ctx_sticky(const sv_ctx* c) { return c->sticky; }
+}  // namespace svqe
 
 sv_status sv_ham_free(sv_ham* H) {
   if (!H) return SV_OK;

@@ -26,6 +26,11 @@ sv_status adjoint_core(sv_ctx* c, const HostCircuit& hc, const sv_ham* H,
 sv_status vqe_enqueue(sv_ctx* c, const HostCircuit& hc, const sv_ham* H, const double* theta_in,
                       double lr, int32_t n_steps, double* theta_out, double* energy_out);
 cudaStream_t ctx_stream(sv_ctx* c);
+// Replace the Pauli sum held by H (lowered for c's register), reusing H's device buffers when
+// they are large enough, so that a pooled context takes a new request without allocating.
+sv_status ham_reload(sv_ctx* c, sv_ham* H, const sv_paulisum* h);
+// True once a CUDA error has made the context unusable.
+bool ctx_sticky(const sv_ctx* c);
 
 // Batched-kernel helpers: team class of an n-qubit instance, teams per CTA of that class,
 // work items from per-instance costs, and the FP64 flop count of one instance.

@@ -9,6 +9,12 @@
 //     kernel (per-instance step counts, steps and trajectory offsets);
 //   * runs large requests on their own context and stream, concurrently with those launches;
 //   * detects completion with events, copies results back and frees the request's memory.
+// A finished large request's context (state buffers, stream, Hamiltonian buffers, completion
+// event and pinned result buffer) is kept idle for the next request of the same qubit count:
+// device and pinned allocations and frees synchronise the whole GPU, so a request that
+// allocated on admission or freed on completion would stall every request in flight.  Idle
+// contexts count against the budget and are freed, oldest first, only when an admission needs
+// their room.
 // The arena is managed by a first-fit allocator with coalescing over 768-byte units (a
 // multiple of every record size the batched kernel indexes, so byte offsets convert exactly
 // to element offsets).
@@ -122,6 +128,18 @@ struct Req {
   sv_ham* ham = nullptr;
   cudaEvent_t ev = nullptr;
   double* pin = nullptr;
+  size_t pin_cap = 0;
+};
+
+// The device resources of a finished large request, kept for the next request of width n.
+struct Idle {
+  int n = 0;
+  uint64_t bytes = 0;  // charged against the budget while idle
+  sv_ctx* ctx = nullptr;
+  sv_ham* ham = nullptr;
+  cudaEvent_t ev = nullptr;
+  double* pin = nullptr;
+  size_t pin_cap = 0;
 };
 
 // Byte layout of a small request's arena block.
@@ -190,6 +208,8 @@ struct sv_server {
   cudaStream_t ustream = nullptr;  // request uploads (never waits for a launch in flight)
   cudaEvent_t bev = nullptr;
   uint64_t used = 0;
+  std::deque<Idle> idle;     // oldest first
+  uint64_t idle_bytes = 0;
 };
 
 namespace {
@@ -282,10 +302,50 @@ void finish(sv_server* s, Req& r, int state, sv_status st, const char* msg) {
   else if (state == Q_CANCELLED) ++s->stats.cancelled;
 }
 
+void free_idle(Idle& d) {
+  if (d.ham) sv_ham_free(d.ham);
+  if (d.ctx) sv_destroy(d.ctx);
+  if (d.ev) cudaEventDestroy(d.ev);
+  if (d.pin) cudaFreeHost(d.pin);
+  d = Idle{};
+}
+
+// Free idle contexts of widths other than keep_n, oldest first, while `need` more bytes would
+// not fit the budget.
+void evict_idle(sv_server* s, uint64_t need, int keep_n) {
+  for (auto it = s->idle.begin();
+       it != s->idle.end() && s->used + s->idle_bytes + need > s->cfg.hbm_budget_bytes;) {
+    if (it->n == keep_n) {
+      ++it;
+      continue;
+    }
+    s->idle_bytes -= it->bytes;
+    free_idle(*it);
+    it = s->idle.erase(it);
+  }
+}
+
 void release(sv_server* s, Req& r) {
   if (r.block >= 0) {
     s->alloc.release(r.block);
     r.block = -1;
+  }
+  if (r.ctx && r.ham && r.ev && r.pin && !ctx_sticky(r.ctx)) {
+    // keep the resources for the next request of this width
+    Idle d;
+    d.n = r.n;
+    d.bytes = r.footprint;
+    d.ctx = r.ctx;
+    d.ham = r.ham;
+    d.ev = r.ev;
+    d.pin = r.pin;
+    d.pin_cap = r.pin_cap;
+    s->idle.push_back(d);
+    s->idle_bytes += d.bytes;
+    r.ctx = nullptr;
+    r.ham = nullptr;
+    r.ev = nullptr;
+    r.pin = nullptr;
   }
   if (r.ham) { sv_ham_free(r.ham); r.ham = nullptr; }
   if (r.ctx) { sv_destroy(r.ctx); r.ctx = nullptr; }
@@ -293,19 +353,45 @@ void release(sv_server* s, Req& r) {
   if (r.pin) { cudaFreeHost(r.pin); r.pin = nullptr; }
   if (r.state != Q_QUEUED) s->used -= r.footprint;
   s->stats.bytes_in_use = s->used;
+  // at most max_active_large idle contexts
+  while ((int)s->idle.size() > s->cfg.max_active_large) {
+    s->idle_bytes -= s->idle.front().bytes;
+    free_idle(s->idle.front());
+    s->idle.pop_front();
+  }
 }
 
-// Start a large request: context, Hamiltonian, all its steps enqueued on its own stream.
+// Start a large request: context, Hamiltonian, all its steps enqueued on its own stream.  An
+// idle context of the same width is reused when there is one (no allocation then).
 sv_status start_large(sv_server* s, Req& r) {
-  sv_status st = sv_create(&r.ctx, r.n, nullptr);
-  if (st != SV_OK) return st;
+  for (auto it = s->idle.begin(); it != s->idle.end(); ++it) {
+    if (it->n != r.n) continue;
+    r.ctx = it->ctx;
+    r.ham = it->ham;
+    r.ev = it->ev;
+    r.pin = it->pin;
+    r.pin_cap = it->pin_cap;
+    s->idle_bytes -= it->bytes;
+    s->idle.erase(it);
+    break;
+  }
+  sv_status st;
+  if (!r.ctx && (st = sv_create(&r.ctx, r.n, nullptr)) != SV_OK) return st;
   if ((st = sv_init_reference(r.ctx, r.ref)) != SV_OK) return st;
   sv_paulisum ps{r.n, (int32_t)r.hcoef.size(), r.hx.data(), r.hz.data(), r.hcoef.data()};
-  if ((st = sv_ham_upload(r.ctx, &ps, &r.ham)) != SV_OK) return st;
+  if ((st = r.ham ? ham_reload(r.ctx, r.ham, &ps) : sv_ham_upload(r.ctx, &ps, &r.ham)) != SV_OK)
+    return st;
   const size_t pin_n = (size_t)r.hc.n_params + (size_t)std::max(1, r.steps);
-  cudaError_t e = cudaMallocHost((void**)&r.pin, pin_n * sizeof(double));
-  if (e != cudaSuccess) return fail_cuda("pinned result buffer", e);
-  if ((e = cudaEventCreateWithFlags(&r.ev, cudaEventDisableTiming)) != cudaSuccess)
+  cudaError_t e;
+  if (r.pin_cap < pin_n) {
+    if (r.pin) cudaFreeHost(r.pin);
+    r.pin = nullptr;
+    r.pin_cap = 0;
+    if ((e = cudaMallocHost((void**)&r.pin, pin_n * sizeof(double))) != cudaSuccess)
+      return fail_cuda("pinned result buffer", e);
+    r.pin_cap = pin_n;
+  }
+  if (!r.ev && (e = cudaEventCreateWithFlags(&r.ev, cudaEventDisableTiming)) != cudaSuccess)
     return fail_cuda("event", e);
   if ((st = vqe_enqueue(r.ctx, r.hc, r.ham, r.theta.data(), r.lr, r.steps, r.pin,
                         r.pin + r.hc.n_params)) != SV_OK)
@@ -328,7 +414,17 @@ void admit(sv_server* s) {
     if (s->cfg.serial && running_small + running_large > 0) break;
     bool slot = r.small ? running_small < s->cfg.max_active_small
                         : running_large < s->cfg.max_active_large;
-    bool fits = slot && s->used + r.footprint <= s->cfg.hbm_budget_bytes;
+    // an idle context of this width is taken over with the bytes it already holds
+    uint64_t mine = 0;
+    if (slot && !r.small)
+      for (const Idle& d : s->idle)
+        if (d.n == r.n) {
+          mine = d.bytes;
+          break;
+        }
+    const uint64_t need = r.footprint > mine ? r.footprint - mine : 0;
+    if (slot) evict_idle(s, need, r.small ? -1 : r.n);
+    bool fits = slot && s->used + s->idle_bytes + need <= s->cfg.hbm_budget_bytes;
     if (fits && r.small) {
       r.block = s->alloc.alloc((int64_t)r.footprint);
       fits = r.block >= 0;
@@ -338,6 +434,7 @@ void admit(sv_server* s) {
       ++it;
       continue;
     }
+    if (!r.small) r.footprint = std::max(r.footprint, mine);
     s->used += r.footprint;
     s->stats.bytes_in_use = s->used;
     s->stats.peak_bytes_in_use = std::max(s->stats.peak_bytes_in_use, (uint64_t)s->used);
@@ -517,7 +614,7 @@ sv_status sv_server_create(const sv_server_config* cfg, sv_server** out) {
   if (!s->cfg.hbm_budget_bytes) s->cfg.hbm_budget_bytes = 4ull << 30;
   if (s->cfg.max_active_small <= 0) s->cfg.max_active_small = 4096;
   if (s->cfg.steps_per_tick <= 0) s->cfg.steps_per_tick = 1;
-  if (s->cfg.max_active_large <= 0) s->cfg.max_active_large = 4;
+  if (s->cfg.max_active_large <= 0) s->cfg.max_active_large = 8;
   if (s->cfg.serial) { s->cfg.max_active_small = 1; s->cfg.max_active_large = 1; }
   s->t0 = std::chrono::steady_clock::now();
   cudaGetDevice(&s->device);
@@ -680,6 +777,8 @@ sv_status sv_server_destroy(sv_server* s) {
   if (s->worker.joinable()) s->worker.join();
   cudaSetDevice(s->device);
   if (s->bstream) cudaStreamSynchronize(s->bstream);
+  for (Idle& d : s->idle) free_idle(d);
+  s->idle.clear();
   cudaFree(s->arena);
   cudaFree(s->d_inst);
   cudaFree(s->d_items);

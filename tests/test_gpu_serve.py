@@ -100,3 +100,32 @@ def test_failure_paths_are_host_side_statuses():
     assert info.status == 0
     assert srv.stats().cancelled == 1
     srv.close()
+
+
+def test_idle_contexts_are_reused_and_evicted_within_the_budget():
+    """Large requests leave their buffers idle for the next request of the same width; a
+    request of another width that needs the room evicts them.  Results are bit for bit those
+    of a fresh server, and the budget holds throughout."""
+    reqs = [dict(W.hea_instance(15, 2, 40, s), steps=3, lr=0.02) for s in (1, 2)]
+    reqs += [dict(W.hea_instance(16, 2, 40, 3), steps=3, lr=0.02)]
+    reqs += [dict(W.hea_instance(15, 2, 40, 4), steps=3, lr=0.02)]
+    fresh = []
+    for r in reqs:
+        one = svqe.Server(serial=True)
+        th, es, info = one.wait(one.submit(r, r["steps"], r["lr"]), 120000)
+        one.close()
+        fresh.append((th, es, info.footprint_bytes))
+    fp15 = max(f[2] for f, r in zip(fresh, reqs) if r["circuit"]["n"] == 15)
+    fp16 = fresh[2][2]
+    budget = fp16 + fp15 // 2  # one request at a time; an idle 15-qubit set must go for n = 16
+    srv = svqe.Server(hbm_budget_bytes=budget, serial=True)
+    for r, (th0, es0, _) in zip(reqs, fresh):
+        th, es, info = srv.wait(srv.submit(r, r["steps"], r["lr"]), 120000)
+        assert info.status == 0
+        assert np.array_equal(th, th0) and np.array_equal(es, es0), r["name"]
+    theta = np.array(reqs[3]["theta"], dtype=np.float64)
+    e0, _ = oracle.energy_grad(reqs[3], theta)
+    assert_energy(fresh[3][1][0], e0, reqs[3]["ham"], "reused context, step 0")
+    st = srv.stats()
+    assert st.completed == len(reqs) and st.peak_bytes_in_use <= budget
+    srv.close()
