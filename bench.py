@@ -55,6 +55,10 @@ def parse():
                     help="single: autotune the fused tile size first (sv_set_autotune)")
     ap.add_argument("--per-circuit-sample", type=int, default=512,
                     help="batch: instances timed through the one-circuit-per-launch path")
+    ap.add_argument("--no-batch-autotune", dest="batch_autotune", action="store_false",
+                    help="batch: use the fixed layout rule instead of letting the layout tuner "
+                         "pick each qubit count's team size and segment widths "
+                         "(sv_batch_set_autotune) before the timed steps")
     ap.add_argument("--no-extras", action="store_true",
                     help="batch: skip the FP64 probe, the 26-qubit kernel table and the "
                          "serving sample that the default line carries")
@@ -789,7 +793,15 @@ def main():
     idx = replica_indices(rank, args.instances)
     insts = W.hea_batch(args.instances * world, seed=args.seed, indices=idx)
     stream = torch.cuda.Stream()
+    tune_s = None
+    if args.batch_autotune:
+        svqe.batch_set_autotune(True)
+        t0 = time.perf_counter()
     batch = svqe.Batch(insts, stream=stream.cuda_stream)
+    if args.batch_autotune:
+        tune_s = time.perf_counter() - t0
+        svqe.batch_set_autotune(False)
+    layout = {n: batch.layout(n) for n in range(4, 13) if batch.layout(n)[0]}
     theta_h = batch.theta_of(insts)
     P = batch.n_params
     theta = torch.tensor(theta_h, dtype=torch.float64, device="cuda")
@@ -872,6 +884,10 @@ def main():
                      "flops_per_launch": flops, "hbm_bytes_per_launch": hbm_bytes},
         "clocks": clocks,
         "wall_s_incl_l2_flush": wall,
+        "layout": {"tuned": bool(args.batch_autotune), "tuning_s": tune_s,
+                   "per_qubits": {str(n): {"team_warps": w, "min_layer": ml,
+                                           "min_diag_rz": md}
+                                  for n, (w, ml, md) in layout.items()}},
     }
     if world == 1 and args.per_circuit_sample > 0:
         pc = per_circuit(insts, args.per_circuit_sample)

@@ -253,6 +253,32 @@ typedef struct {
 sv_status sv_batch_create(const sv_instance* inst, int32_t n, void* cuda_stream,
                           sv_batch** out);
 sv_status sv_batch_free(sv_batch* b);
+/* Layout autotuner of the batched kernel (process-wide; off by default).  The kernel's layout
+ * for the instances of one qubit count q is the number of warps that run each instance and the
+ * widths at which runs of gates become segments: a run of RY/RX gates on distinct qubits is
+ * one commuting-layer segment, and a run of RZ/CZ gates one diagonal segment, only when it is
+ * long enough; shorter runs are applied gate by gate (see sv_batch_segments).  Off, every batch
+ * uses a fixed rule (the smallest team that holds the instance; layers of >= 2 gates and
+ * diagonal runs of >= 3 RZ gates become segments).  On, sv_batch_create first measures, for
+ * each qubit count of the batch not measured before in this process, the candidate layouts
+ * (that team and the one with twice its warps; layer segments on or off; diagonal segments on
+ * or off) on a calibration batch made of that count's instances, and compiles the batch with
+ * the fastest.  The results are cached for the process and, if the environment variable
+ * SVQE_BATCH_TUNE_CACHE names a file, read from and appended to that file.  The tuning runs
+ * on the batch's stream and synchronises it; call it outside any stream capture. */
+sv_status sv_batch_set_autotune(int32_t enable);
+/* Put a layout for n_qubits-qubit instances into the tuner's process-wide cache, so that
+ * batches created while the tuner is on use it without measuring: team_warps (1, 2, 4 or 8;
+ * 2^n_qubits <= 512 x team_warps), and the two segment widths (>= 1).  team_warps = 0 removes
+ * the entry, so that the next tuned batch measures that size again.  SV_EINVAL for a layout
+ * that cannot hold the instances.  Host-only. */
+sv_status sv_batch_set_layout(int32_t n_qubits, int32_t team_warps, int32_t min_layer,
+                              int32_t min_diag_rz);
+/* The layout b was compiled with for n_qubits-qubit instances: warps per instance team and the
+ * two segment widths (a width of 2^20 means that segment kind is not used).  All three are 0
+ * when b holds no instance of that size.  Host-only.  Any output pointer may be NULL. */
+sv_status sv_batch_layout(const sv_batch* b, int32_t n_qubits, int32_t* team_warps,
+                          int32_t* min_layer, int32_t* min_diag_rz);
 /* Sizes: instances, total parameters. */
 sv_status sv_batch_info(const sv_batch* b, int32_t* n_instances, int64_t* n_params_total);
 /* Algorithmic cost of one sv_batch_run, counted from the compiled segments exactly as the

@@ -3,9 +3,11 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <map>
 #include <mutex>
 #include <new>
 #include <numeric>
@@ -119,6 +121,8 @@ struct sv_batch {
   // CUDA graph of [counter reset, persistent kernel] for one set of device pointers
   cudaGraphExec_t exec = nullptr;
   const void* key[3] = {nullptr, nullptr, nullptr};
+  // layout per qubit count (team class, segment widths); cls < 0: no instance of that count
+  BLayout lay[SV_BATCH_MAX_QUBITS + 1];
 };
 
 // ------------------------------------------------------------------------------ helpers
@@ -1001,23 +1005,30 @@ int svqe::batch_class(int n) {
   return n <= kClassQubits[2] ? 2 : n <= kClassQubits[3] ? 3 : n <= kClassQubits[1] ? 1 : 0;
 }
 int svqe::class_teams(int n) { return 8 / kClassWarps[batch_class(n)]; }
+BLayout svqe::default_layout(int n) { return BLayout{batch_class(n), 2, 3}; }
 
-// Work items: one instance per team of its class (one, two, eight or four per item).  What sets an item's duration is the work of one thread of its slowest team,
-// not the item's flops (eight 9-qubit instances on one warp each take about as long as one
-// 12-qubit instance on eight warps), so instances are ordered by that estimate -- amplitudes per
-// thread times the per-amplitude work of the ops and groups, plus a per-op latency term -- and
-// items by the estimate of their first (slowest) instance, slowest first.
-static double thread_time(const BInst& B, double cost) {
-  const int team = 32 * kClassWarps[batch_class(B.n)];
+// Work items: one instance per team of its class (one, two, eight or four per item).  What
+// sets an item's duration is the work of one thread of its slowest team, not the item's flops
+// (eight 9-qubit instances on one warp each take about as long as one 12-qubit instance on
+// eight warps), so instances are ordered by that estimate -- amplitudes per thread times the
+// per-amplitude work of the ops and groups, plus a per-op latency term -- and items by the
+// estimate of their first (slowest) instance, slowest first.
+static double thread_time(const BInst& B, int cls) {
+  const int team = 32 * kClassWarps[cls];
   const double per_thread = std::max(1.0, (double)(1u << B.n) / team);
-  (void)cost;
   return per_thread * (6.0 * B.n_ops + 2.0 * B.n_groups + 8.0) + 150.0 * B.n_ops;
 }
 
-std::vector<BItem> svqe::batch_items(const std::vector<BInst>& bi, const std::vector<double>& cost_in) {
+std::vector<BItem> svqe::batch_items(const std::vector<BInst>& bi,
+                                     const std::vector<double>& cost_in, const int* cls_of_n) {
+  (void)cost_in;
   const int n = (int)bi.size();
+  std::vector<int> cls(n);
   std::vector<double> cost(n);
-  for (int i = 0; i < n; ++i) cost[i] = thread_time(bi[i], cost_in[i]);
+  for (int i = 0; i < n; ++i) {
+    cls[i] = cls_of_n ? cls_of_n[bi[i].n] : batch_class(bi[i].n);
+    cost[i] = thread_time(bi[i], cls[i]);
+  }
   std::vector<int> order(n);
   std::iota(order.begin(), order.end(), 0);
   std::stable_sort(order.begin(), order.end(), [&](int a, int c) { return cost[a] > cost[c]; });
@@ -1033,7 +1044,7 @@ std::vector<BItem> svqe::batch_items(const std::vector<BInst>& bi, const std::ve
   }
   std::vector<double> first_cost(kNumClasses, 0.0);
   for (int i : order) {
-    const int c = batch_class(bi[i].n);
+    const int c = cls[i];
     if (fill[c] == 0) first_cost[c] = cost[i];
     open[c].inst[fill[c]++] = i;
     if (fill[c] == cap[c]) {
@@ -1119,10 +1130,19 @@ sv_status sv_batch_free(sv_batch* b) {
   return SV_OK;
 }
 
-sv_status sv_batch_create(const sv_instance* inst, int32_t n, void* stream, sv_batch** out) {
-  clear_error();
-  if (!out || (n > 0 && !inst) || n < 1) { set_error("bad arguments (n = %d)", n); return SV_EINVAL; }
+// Compile and upload a batch with the given layout per qubit count (lay[q] for q-qubit
+// instances; a class that cannot hold a q-qubit instance falls back to the fixed rule).
+static sv_status batch_build(const sv_instance* inst, int32_t n, void* stream,
+                             const BLayout* lay_in, sv_batch** out) {
   *out = nullptr;
+  BLayout lay[SV_BATCH_MAX_QUBITS + 1];
+  int cls_of_n[SV_BATCH_MAX_QUBITS + 1];
+  for (int q = 0; q <= SV_BATCH_MAX_QUBITS; ++q) {
+    lay[q] = lay_in ? lay_in[q] : default_layout(q);
+    if (lay[q].cls < 0 || lay[q].cls >= kNumClasses || q > kClassQubits[lay[q].cls])
+      lay[q].cls = batch_class(q);
+    cls_of_n[q] = lay[q].cls;
+  }
   std::vector<BInst> bi(n);
   std::vector<DOp> ops;
   std::vector<DGroup> groups;
@@ -1147,7 +1167,7 @@ sv_status sv_batch_create(const sv_instance* inst, int32_t n, void* stream, sv_b
     if ((st = lower_ham(&I.ham, I.circuit.n_qubits, kTableBitsBatch, hh)) != SV_OK) return st;
     if (I.ref >= (1ull << hc.n)) { set_error("instance %d: reference index out of range", i); return SV_EINVAL; }
     std::vector<Seg> sg;
-    const int n_ckpt = segment_ops(hc.ops, 2, 3, sg);
+    const int n_ckpt = segment_ops(hc.ops, lay[hc.n].min_layer, lay[hc.n].min_diag_rz, sg);
     const double inst_flops = batch_instance_flops(hc, hh, sg);
     flops += inst_flops;
     bytes += (double)hc.ops.size() * (sizeof(DOp) + sizeof(Rot) * 2 + 2 * sizeof(double)) +
@@ -1175,7 +1195,8 @@ sv_status sv_batch_create(const sv_instance* inst, int32_t n, void* stream, sv_b
     B.pp_off = (int64_t)pptr.size();
     theta_off += hc.n_params;
     // a CTA's checkpoint region is split evenly among the teams of the instance's class
-    ckpt_slot = std::max<int64_t>(ckpt_slot, team_ckpt_amps(n_ckpt, hc.n) * class_teams(hc.n));
+    ckpt_slot = std::max<int64_t>(ckpt_slot, team_ckpt_amps(n_ckpt, hc.n) *
+                                                  (8 / kClassWarps[lay[hc.n].cls]));
     segs.insert(segs.end(), sg.begin(), sg.end());
     // parameter -> ops using it, in op order (CSR)
     std::vector<std::vector<int32_t>> uses(hc.n_params);
@@ -1214,8 +1235,10 @@ sv_status sv_batch_create(const sv_instance* inst, int32_t n, void* stream, sv_b
     if (e != cudaSuccess) { set_error("cudaStreamCreate: %s", cudaGetErrorString(e)); delete b; return SV_ECUDA; }
     b->own_stream = true;
   }
-  const std::vector<BItem> items = batch_items(bi, cost);
+  const std::vector<BItem> items = batch_items(bi, cost, cls_of_n);
   b->n_items = (int)items.size();
+  for (int q = 0; q <= SV_BATCH_MAX_QUBITS; ++q) b->lay[q] = BLayout{-1, 0, 0};
+  for (int i = 0; i < n; ++i) b->lay[bi[i].n] = lay[bi[i].n];
   auto alloc = [&](void** p, size_t bytes) {
     return cudaMalloc(p, std::max<size_t>(bytes, 16)) == cudaSuccess;
   };
@@ -1268,6 +1291,202 @@ sv_status sv_batch_create(const sv_instance* inst, int32_t n, void* stream, sv_b
   }
   *out = b;
   return SV_OK;
+}
+
+// ------------------------------------------------------------------------------ layout tuner
+// The batched kernel's layout for q-qubit instances (BLayout) trades threads per instance
+// against instances per CTA, and per-segment set-up work (tables, checkpoints, staged gates)
+// against per-gate passes; which wins depends on q.  With sv_batch_set_autotune(1),
+// sv_batch_create measures, for every qubit count of the batch that the process-wide cache
+// does not hold yet, each candidate layout (the smallest team that holds the instance and the
+// next larger one, times commuting-layer segments on or off, times diagonal segments on or off)
+// on a calibration batch: that count's instances of the batch, repeated to give every CTA two
+// items.  One warm-up and three timed runs of the persistent launch (CUDA events on the batch's
+// stream); the fastest layout is kept.  The cache is optionally kept in the text file named by
+// SVQE_BATCH_TUNE_CACHE, one "q cls min_layer min_diag_rz" line per qubit count.
+static std::mutex g_btune_mu;
+static std::map<int, BLayout> g_btune;
+static bool g_btune_loaded = false;
+static std::atomic<int> g_batch_tune{0};
+constexpr int kSegOff = 1 << 20;  // a width no run reaches: that segment kind is not used
+
+static sv_status time_batch(sv_batch* b, float* best_ms) {
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  cudaError_t e = cudaSuccess;
+  if ((e = cudaEventCreate(&e0)) != cudaSuccess || (e = cudaEventCreate(&e1)) != cudaSuccess) {
+    if (e0) cudaEventDestroy(e0);
+    set_error("cudaEventCreate: %s", cudaGetErrorString(e));
+    return SV_ECUDA;
+  }
+  sv_status st = SV_OK;
+  if (cudaMemsetAsync(b->theta, 0, (size_t)std::max<int64_t>(b->total_params, 1) * 8,
+                      b->stream) != cudaSuccess) {
+    set_error("tuner: theta reset failed");
+    st = SV_ECUDA;
+  }
+  *best_ms = 1e30f;
+  for (int rep = 0; rep < 4 && st == SV_OK; ++rep) {
+    float ms = 0.0f;
+    if (cudaEventRecord(e0, b->stream) != cudaSuccess ||
+        (st = sv_batch_run_dev(b, b->theta, b->energy, b->grad)) != SV_OK ||
+        cudaEventRecord(e1, b->stream) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+        cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) {
+      if (st == SV_OK) {
+        set_error("tuner: timing failed");
+        st = SV_ECUDA;
+      }
+      break;
+    }
+    if (rep > 0) *best_ms = std::min(*best_ms, ms);
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  return st;
+}
+
+static sv_status tune_layouts(const sv_instance* inst, int32_t n, void* stream, BLayout* lay) {
+  std::vector<int> by_q[SV_BATCH_MAX_QUBITS + 1];
+  for (int i = 0; i < n; ++i) {
+    const int q = inst[i].circuit.n_qubits;
+    if (q >= 1 && q <= SV_BATCH_MAX_QUBITS) by_q[q].push_back(i);
+  }
+  const char* path = std::getenv("SVQE_BATCH_TUNE_CACHE");
+  {
+    std::lock_guard<std::mutex> lk(g_btune_mu);
+    if (!g_btune_loaded) {
+      g_btune_loaded = true;
+      if (path) {
+        if (FILE* f = std::fopen(path, "r")) {
+          int q = 0, c = 0, ml = 0, md = 0;
+          while (std::fscanf(f, "%d %d %d %d", &q, &c, &ml, &md) == 4)
+            if (q >= 1 && q <= SV_BATCH_MAX_QUBITS && c >= 0 && c < kNumClasses &&
+                q <= kClassQubits[c] && ml >= 1 && md >= 1)
+              g_btune[q] = BLayout{c, ml, md};
+          std::fclose(f);
+        }
+      }
+    }
+  }
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+    set_error("cudaDeviceGetAttribute failed");
+    return SV_ECUDA;
+  }
+  for (int q = 1; q <= SV_BATCH_MAX_QUBITS; ++q) {
+    if (by_q[q].empty()) continue;
+    {
+      std::lock_guard<std::mutex> lk(g_btune_mu);
+      const auto it = g_btune.find(q);
+      if (it != g_btune.end()) {
+        lay[q] = it->second;
+        continue;
+      }
+    }
+    // candidate team classes: the fixed rule's, and the class with twice its warps if it exists
+    std::vector<int> classes{batch_class(q)};
+    for (int c = 0; c < kNumClasses; ++c)
+      if (kClassWarps[c] == 2 * kClassWarps[classes[0]]) classes.push_back(c);
+    const int teams = 8 / kClassWarps[classes[0]];
+    const int m = 2 * sms * teams;
+    std::vector<sv_instance> cal(m);
+    for (int k = 0; k < m; ++k) cal[k] = inst[by_q[q][k % by_q[q].size()]];
+    BLayout best = default_layout(q);
+    float best_ms = 1e30f;
+    for (int c : classes)
+      for (int ml : {2, kSegOff})
+        for (int md : {3, kSegOff}) {
+          BLayout L[SV_BATCH_MAX_QUBITS + 1];
+          for (int r = 0; r <= SV_BATCH_MAX_QUBITS; ++r) L[r] = default_layout(r);
+          L[q] = BLayout{c, ml, md};
+          sv_batch* b = nullptr;
+          sv_status st = batch_build(cal.data(), m, stream, L, &b);
+          if (st == SV_ENOMEM) {  // a layout that does not fit is not a candidate
+            cudaGetLastError();
+            continue;
+          }
+          if (st != SV_OK) return st;
+          float ms = 0.0f;
+          st = time_batch(b, &ms);
+          sv_batch_free(b);
+          if (st != SV_OK) return st;
+          if (ms < best_ms) {
+            best_ms = ms;
+            best = L[q];
+          }
+        }
+    lay[q] = best;
+    std::lock_guard<std::mutex> lk(g_btune_mu);
+    g_btune[q] = best;
+    if (path) {
+      if (FILE* f = std::fopen(path, "a")) {
+        std::fprintf(f, "%d %d %d %d\n", q, best.cls, best.min_layer, best.min_diag_rz);
+        std::fclose(f);
+      }
+    }
+  }
+  return SV_OK;
+}
+
+sv_status sv_batch_set_autotune(int32_t enable) {
+  clear_error();
+  g_batch_tune.store(enable ? 1 : 0);
+  return SV_OK;
+}
+
+sv_status sv_batch_set_layout(int32_t n_qubits, int32_t team_warps, int32_t min_layer,
+                              int32_t min_diag_rz) {
+  clear_error();
+  if (n_qubits < 1 || n_qubits > SV_BATCH_MAX_QUBITS) {
+    set_error("n_qubits %d outside [1, %d]", n_qubits, SV_BATCH_MAX_QUBITS);
+    return SV_EINVAL;
+  }
+  std::lock_guard<std::mutex> lk(g_btune_mu);
+  if (team_warps == 0) {
+    g_btune.erase(n_qubits);
+    return SV_OK;
+  }
+  int cls = -1;
+  for (int c = 0; c < kNumClasses; ++c)
+    if (kClassWarps[c] == team_warps) cls = c;
+  if (cls < 0 || n_qubits > kClassQubits[cls] || min_layer < 1 || min_diag_rz < 1) {
+    set_error("layout (%d warps, widths %d, %d) cannot run %d-qubit instances", team_warps,
+              min_layer, min_diag_rz, n_qubits);
+    return SV_EINVAL;
+  }
+  g_btune[n_qubits] = BLayout{cls, min_layer, min_diag_rz};
+  return SV_OK;
+}
+
+sv_status sv_batch_layout(const sv_batch* b, int32_t n_qubits, int32_t* team_warps,
+                          int32_t* min_layer, int32_t* min_diag_rz) {
+  clear_error();
+  if (!b || n_qubits < 1 || n_qubits > SV_BATCH_MAX_QUBITS) {
+    set_error("NULL handle or n_qubits %d outside [1, %d]", n_qubits, SV_BATCH_MAX_QUBITS);
+    return SV_EINVAL;
+  }
+  const BLayout& L = b->lay[n_qubits];
+  const bool used = L.cls >= 0;
+  if (team_warps) *team_warps = used ? kClassWarps[L.cls] : 0;
+  if (min_layer) *min_layer = used ? L.min_layer : 0;
+  if (min_diag_rz) *min_diag_rz = used ? L.min_diag_rz : 0;
+  return SV_OK;
+}
+
+sv_status sv_batch_create(const sv_instance* inst, int32_t n, void* stream, sv_batch** out) {
+  clear_error();
+  if (!out || (n > 0 && !inst) || n < 1) { set_error("bad arguments (n = %d)", n); return SV_EINVAL; }
+  *out = nullptr;
+  BLayout lay[SV_BATCH_MAX_QUBITS + 1];
+  for (int q = 0; q <= SV_BATCH_MAX_QUBITS; ++q) lay[q] = default_layout(q);
+  if (g_batch_tune.load()) {
+    for (int i = 0; i < n; ++i)  // invalid instances are reported by batch_build, untuned
+      if (inst[i].circuit.n_qubits < 1 || inst[i].circuit.n_qubits > SV_BATCH_MAX_QUBITS)
+        return batch_build(inst, n, stream, lay, out);
+    const sv_status st = tune_layouts(inst, n, stream, lay);
+    if (st != SV_OK) return st;
+  }
+  return batch_build(inst, n, stream, lay, out);
 }
 
 sv_status sv_batch_cost(const sv_batch* b, double* fp64_flops, double* hbm_bytes) {

@@ -32,11 +32,26 @@ sv_status ham_reload(sv_ctx* c, sv_ham* H, const sv_paulisum* h);
 // True once a CUDA error has made the context unusable.
 bool ctx_sticky(const sv_ctx* c);
 
-// Batched-kernel helpers: team class of an n-qubit instance, teams per CTA of that class,
-// work items from per-instance costs, and the FP64 flop count of one instance.
+// Layout of the batched kernel for the instances of one qubit count: the team class of their
+// work items (kClassWarps) and the segment widths their circuits are cut with (segment_ops: a
+// run of RY/RX gates on distinct qubits becomes a commuting-layer segment when it has at least
+// min_layer gates, a run of RZ/CZ a diagonal segment when it has at least min_diag_rz RZ
+// gates; shorter runs are applied gate by gate).
+struct BLayout {
+  int cls;
+  int min_layer;
+  int min_diag_rz;
+};
+// The fixed rule: the smallest team that holds the instance, widths 2 and 3.
+BLayout default_layout(int n);
+
+// Batched-kernel helpers: team class of an n-qubit instance under the fixed rule, teams per CTA
+// of that class, work items from per-instance costs (cls_of_n: team class per qubit count, or
+// nullptr for the fixed rule), and the FP64 flop count of one instance.
 int batch_class(int n);
 int class_teams(int n);
-std::vector<BItem> batch_items(const std::vector<BInst>& bi, const std::vector<double>& cost);
+std::vector<BItem> batch_items(const std::vector<BInst>& bi, const std::vector<double>& cost,
+                               const int* cls_of_n = nullptr);
 double batch_instance_flops(const HostCircuit& hc, const HostHam& hh,
                             const std::vector<Seg>& segs);
 

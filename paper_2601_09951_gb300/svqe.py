@@ -100,6 +100,9 @@ def lib():
         "sv_batch_adam_dev": ([P, P, dbl, i32, P, i32], i32),
         "sv_adjoint_grad_noalloc": ([P, u64, i32, P, i32, P, i64, P, P, P, P], i32),
         "sv_fp64_probe": ([i32, i32, i32, i32, P, P, P], i32),
+        "sv_batch_set_autotune": ([i32], i32),
+        "sv_batch_layout": ([P, i32, P, P, P], i32),
+        "sv_batch_set_layout": ([i32, i32, i32, i32], i32),
         "sv_server_create": ([P, P], i32),
         "sv_server_submit": ([P, P, P, i32, dbl, P], i32),
         "sv_server_wait": ([P, u64, i32, P, P, P], i32),
@@ -246,6 +249,21 @@ def adjoint_grad_noalloc(circuit, ref, ham_n_qubits, groups_ptr, n_groups, table
         C.ref(), int(ref), int(ham_n_qubits), ctypes.c_void_p(groups_ptr), int(n_groups),
         ctypes.c_void_p(tables_ptr), int(n_table), ctypes.c_void_p(theta_ptr),
         ctypes.c_void_p(energy_ptr), ctypes.c_void_p(grad_ptr), _stream_arg(int(stream))))
+
+
+def batch_set_autotune(enable):
+    """sv_batch_set_autotune: process-wide switch of the batched kernel's layout tuner."""
+    _check(lib().sv_batch_set_autotune(1 if enable else 0))
+
+
+def batch_set_layout(n_qubits, team_warps, min_layer, min_diag_rz):
+    """sv_batch_set_layout: pin (or with team_warps = 0 forget) the tuner's layout for one
+    qubit count."""
+    _check(lib().sv_batch_set_layout(int(n_qubits), int(team_warps), int(min_layer),
+                                     int(min_diag_rz)))
+
+
+SEG_OFF = 1 << 20  # a segment width no run reaches: that segment kind is not used
 
 
 def fp64_probe(blocks, threads, chains, iters, out_ptr, stream):
@@ -401,6 +419,14 @@ class Batch:
         ni, npar = ctypes.c_int32(), ctypes.c_int64()
         _check(lib().sv_batch_info(self._b, ctypes.byref(ni), ctypes.byref(npar)))
         self.n_instances, self.n_params = ni.value, npar.value
+
+    def layout(self, n_qubits):
+        """(warps per instance team, min commuting-layer width, min diagonal RZ count) the batch
+        was compiled with for n_qubits-qubit instances (zeros if it holds none)."""
+        w, ml, md = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
+        _check(lib().sv_batch_layout(self._b, int(n_qubits), ctypes.byref(w), ctypes.byref(ml),
+                                     ctypes.byref(md)))
+        return w.value, ml.value, md.value
 
     def cost(self):
         """(FP64 flops, HBM bytes) of one run, from the compiled segments."""

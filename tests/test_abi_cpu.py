@@ -205,3 +205,21 @@ def test_fused_plan_keeps_dependencies_and_fits_tiles(make):
         assert len(bits | low) <= 11, (p, sorted(bits))
     # fusion actually fuses: far fewer passes than gates
     assert n_pass * 3 <= G
+
+
+def test_layout_and_probe_calls_validate_their_arguments():
+    """Host-side argument checks of the layout tuner's calls and the FP64 probe (no device
+    work: every call below is rejected before a launch)."""
+    for bad in ((0, 1, 2, 3), (13, 8, 2, 3), (10, 1, 2, 3), (12, 4, 2, 3), (5, 3, 2, 3),
+                (5, 1, 0, 3), (5, 1, 2, 0)):
+        with pytest.raises(svqe.SvError) as e:
+            svqe.batch_set_layout(*bad)
+        assert e.value.status == svqe.SV_EINVAL, bad
+    svqe.batch_set_layout(9, 2, svqe.SEG_OFF, 3)  # valid: pinned, then forgotten
+    svqe.batch_set_layout(9, 0, 0, 0)
+    L = svqe.lib()
+    assert L.sv_batch_layout(None, 5, None, None, None) == svqe.SV_EINVAL
+    for shape in ((0, 128, 8, 10), (4, 100, 8, 10), (4, 2048, 8, 10), (4, 128, 3, 10),
+                  (4, 128, 8, 0)):
+        assert L.sv_fp64_probe(*shape, ctypes.c_void_p(16), None, None) == svqe.SV_EINVAL
+    assert L.sv_fp64_probe(4, 128, 8, 10, None, None, None) == svqe.SV_EINVAL
