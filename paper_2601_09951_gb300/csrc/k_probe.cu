@@ -4,8 +4,9 @@
 // the rate at which the SMs retire double-precision fused multiply-adds.  This kernel
 // measures that rate: every thread runs CHAINS independent dependency chains
 // x <- fma(x, a, b), so that with enough chains and warps the pipe, not the FMA latency,
-// limits it.  a and b are kernel arguments (the compiler cannot fold the chains), and a < 1
-// keeps every value finite and normal: the chains converge to b / (1 - a).
+// limits it.  a and b are kernel arguments (the compiler cannot fold the chains), and
+// multipliers below 1 keep every value finite and normal: each chain converges to
+// c / (1 - m).
 #include <cuda_runtime.h>
 
 #include "../../include/svqe.h"
@@ -16,17 +17,25 @@ namespace {
 
 template <int CHAINS>
 __global__ void k_fp64_probe(int iters, double a, double b, double* __restrict__ out) {
-  double x[CHAINS];
+  // Each chain has its own multiplier and addend in registers (derived from the thread index,
+  // so the compiler cannot take them from the constant bank or share them), the form the
+  // state-vector kernels' FMAs take.
+  double x[CHAINS], m[CHAINS], c[CHAINS];
 #pragma unroll
-  for (int c = 0; c < CHAINS; ++c) x[c] = (double)(threadIdx.x + c) * 1e-3;
+  for (int k = 0; k < CHAINS; ++k) {
+    const double t = (double)((threadIdx.x + 3 * k) & 15);
+    x[k] = t * 1e-3;
+    m[k] = a - t * 1e-12;
+    c[k] = b + t * 1e-12;
+  }
 #pragma unroll 4
   for (int i = 0; i < iters; ++i) {
 #pragma unroll
-    for (int c = 0; c < CHAINS; ++c) x[c] = fma(x[c], a, b);
+    for (int k = 0; k < CHAINS; ++k) x[k] = fma(x[k], m[k], c[k]);
   }
   double s = 0.0;
 #pragma unroll
-  for (int c = 0; c < CHAINS; ++c) s += x[c];
+  for (int k = 0; k < CHAINS; ++k) s += x[k];
   // one store per thread keeps the chains live; it is not part of the count
   out[(size_t)blockIdx.x * blockDim.x + threadIdx.x] = s;
 }
