@@ -238,17 +238,22 @@ def serve_run(svqe, reqs, rate, serial=False, budget=64 << 30):
     th = threading.Thread(target=submitter)
     th.start()
     th.join()
-    lat = []
-    for rid in ids:
+    lat, busy = [], {}
+    for r, rid in zip(reqs, ids):
         _, _, info = srv.wait(rid, -1)
         lat.append(info.done_s - info.submit_s)
+        # running time by size class (in the serial server: each request's own GPU time)
+        cls = "n<=12" if info.n_qubits <= 12 else "n13-19" if info.n_qubits < 20 else "n20-24"
+        busy[cls] = busy.get(cls, 0.0) + (info.done_s - info.admit_s)
     wall = time.perf_counter() - t0
     st = srv.stats()
     srv.close()
     evals = sum(r["steps"] for r in reqs)
+    tot = sum(busy.values()) or 1.0
     return {"evals_per_s": evals / wall, "p50_ms": 1e3 * float(np.percentile(lat, 50)),
             "p99_ms": 1e3 * float(np.percentile(lat, 99)), "wall_s": wall,
-            "launches": int(st.launches), "peak_bytes": int(st.peak_bytes_in_use)}
+            "launches": int(st.launches), "peak_bytes": int(st.peak_bytes_in_use),
+            "running_time_share": {k: v / tot for k, v in sorted(busy.items())}}
 
 
 def run_serve(args):
