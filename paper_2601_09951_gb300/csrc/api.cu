@@ -557,6 +557,15 @@ static sv_status plan_circuit(sv_ctx* c, const HostCircuit& hc, int tile_bits) {
         return k;
       };
       const uint32_t c0 = P(0);
+      // delta = M^-1 e_0: the linear parts of the gates (a CNOT flips its target where its
+      // control is set; an X is a constant) applied to e_0 in reverse order
+      uint32_t delta = 1u;
+      for (int l = first + len - 1; l >= first + split; --l) {
+        const uint32_t lo = (uint32_t)hc.ops[l].lo_or, fl = (uint32_t)hc.ops[l].flip;
+        if (lo && (delta & lo) == lo) delta ^= fl;
+      }
+      d.pair = delta >> 11;
+      d.pair_hi = d.pair ? 31 - __builtin_clz(d.pair) : 0;
       for (int t = 0; t < 3; ++t)
         for (uint32_t j = 0; j < 2048; ++j) {
           const uint64_t k = (uint64_t)j << (11 * t);

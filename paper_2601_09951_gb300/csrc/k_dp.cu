@@ -57,6 +57,18 @@ __device__ __forceinline__ double2 dp_outer(const DpArgs& a, uint64_t blk) {
   return cmul(a.phase_b1[blk & 1023], a.phase_b2[blk >> 10]);
 }
 
+// The block of visit index t (see DpArgs::pair): bit 0 of t selects pair, bit pair_hi of t
+// selects block bit 0, every other bit of t is the same block bit.  A bijection on the block
+// indices, because pair has bit pair_hi set.
+__device__ __forceinline__ uint64_t dp_block(const DpArgs& a, uint64_t t) {
+  if (a.pair <= 1u) return t;
+  const uint64_t ep = 1ull << a.pair_hi;
+  uint64_t b = t & ~(ep | 1ull);
+  if (t & 1ull) b ^= a.pair;
+  if (t & ep) b ^= 1ull;
+  return b;
+}
+
 __device__ __forceinline__ bool dp_cz(const DpArgs& a, uint64_t k) {
   uint32_t par = 0;
   for (int c = 0; c < a.n_cz; ++c) par ^= ((k & a.cz_mask[c]) == a.cz_mask[c]);
@@ -70,7 +82,8 @@ __global__ void __launch_bounds__(kDT) k_dp_fwd(const double2* __restrict__ in,
   DpShared& S = *reinterpret_cast<DpShared*>(dsm);
   dp_stage(S, a);
   const uint64_t nblk = a.N >> kDB;
-  for (uint64_t blk = blockIdx.x; blk < nblk; blk += gridDim.x) {
+  for (uint64_t t = blockIdx.x; t < nblk; t += gridDim.x) {
+    const uint64_t blk = dp_block(a, t);
     const double2 o = dp_outer(a, blk);
 #pragma unroll
     for (int i = 0; i < kDBlock / kDT; ++i) {
@@ -90,7 +103,8 @@ __global__ void __launch_bounds__(kDT) k_dp_bwd_psi(const double2* __restrict__ 
   DpShared& S = *reinterpret_cast<DpShared*>(dsm);
   dp_stage(S, a);
   const uint64_t nblk = a.N >> kDB;
-  for (uint64_t blk = blockIdx.x; blk < nblk; blk += gridDim.x) {
+  for (uint64_t t = blockIdx.x; t < nblk; t += gridDim.x) {
+    const uint64_t blk = dp_block(a, t);
     const double2 o = dp_outer(a, blk);
 #pragma unroll
     for (int i = 0; i < kDBlock / kDT; ++i) {
@@ -106,9 +120,10 @@ __global__ void __launch_bounds__(kDT) k_dp_bwd_psi(const double2* __restrict__ 
 // Backward, lambda: out[k] = conj(phase(k)) lam[P(k)], and the RZ gradient shares from
 // w_k = Im(conj(out[k]) psi_b[k]) with psi_b the un-phased psi (k_dp_bwd_psi's output):
 // partial[op * kRedBlocks + block] for every parameterised RZ op of the segment.  The first
-// G = min(blocks, 1024) CTAs do the work, CTA c taking blocks c, c + G, c + 2G, ...: block-index
-// bits below log2 G are fixed per CTA (their signs apply to the CTA's total), and the bits
-// above it are bits of the round r (one sum each, at most 10).  The other CTAs write zeros.
+// G = min(blocks, 1024) CTAs do the work, CTA c taking visit indices t = c, c + G, c + 2G, ...
+// (block dp_block(t)): bits of t below log2 G are fixed per CTA (their signs apply to the
+// CTA's total), and the bits above it are bits of the round r (one sum each, at most 10).
+// The other CTAs write zeros.
 __global__ void __launch_bounds__(kDT, 2) k_dp_bwd_lam(const double2* __restrict__ lam,
                                                     const double2* __restrict__ psi_b,
                                                     double2* __restrict__ out, DpArgs a,
@@ -126,7 +141,8 @@ __global__ void __launch_bounds__(kDT, 2) k_dp_bwd_lam(const double2* __restrict
   for (int b = 0; b < kMaxRound; ++b) hr[b] = 0.0;
   if (blockIdx.x < G) {
     uint64_t r = 0;
-    for (uint64_t blk = blockIdx.x; blk < nblk; blk += G, ++r) {
+    for (uint64_t t = blockIdx.x; t < nblk; t += G, ++r) {
+      const uint64_t blk = dp_block(a, t);
       const double2 o = dp_outer(a, blk);
       double wb = 0.0;
 #pragma unroll
@@ -157,13 +173,29 @@ __global__ void __launch_bounds__(kDT, 2) k_dp_bwd_lam(const double2* __restrict
       v = ((tid >> bit) & 1) ? dneg(W) : W;
     } else if (bit < kDB) {
       v = bit == 8 ? mid[0] : bit == 9 ? mid[1] : mid[2];
-    } else if (bit < kDB + lg) {
-      v = ((blockIdx.x >> (bit - kDB)) & 1u) ? dneg(W) : W;
     } else {
-      v = 0.0;
+      // block bit jb of the block visited at t = blockIdx.x + r G is bit src of t, flipped by
+      // t's bit 0 where pair has bit jb (dp_block); bits of t below lg are the CTA's, the
+      // others the round's
+      const int jb = bit - kDB;
+      const bool paired = a.pair > 1u;
+      const bool t0 = blockIdx.x & 1u;
+      int src = jb;
+      bool flip = false;
+      if (paired) {
+        if (jb == a.pair_hi) src = 0;
+        else if (jb == 0) src = a.pair_hi;
+        flip = jb != a.pair_hi && t0 && ((a.pair >> jb) & 1u);
+      }
+      if (src < lg) {
+        v = ((blockIdx.x >> src) & 1u) ? dneg(W) : W;
+      } else {
+        v = 0.0;
 #pragma unroll
-      for (int b = 0; b < kMaxRound; ++b)
-        if (b == bit - kDB - lg) v = hr[b];
+        for (int b = 0; b < kMaxRound; ++b)
+          if (b == src - lg) v = hr[b];
+      }
+      if (flip) v = dneg(v);
     }
     v = warp_sum(v);
     if ((tid & 31) == 0) S.red[tid >> 5] = v;

@@ -76,6 +76,13 @@ struct DpArgs {
   int rz_bit[kDpMaxRz];
   int n_rz_all;              // every RZ op of the diagonal part: phase factors
   int rz_all[kDpMaxRz];
+  // Block pairing of the gather/scatter.  The amplitude P(k) ^ 1, which shares P(k)'s 32-byte
+  // sector, is P(k ^ delta) with delta = M^-1 e_0 (M the linear part of P); pair is the block
+  // part delta >> 11 and pair_hi its highest set bit.  With pair > 1 the kernels visit block
+  // B(t) for t = 0, 1, ..., where B(t) and B(t ^ 1) differ by pair, so adjacent CTAs read (or
+  // write) the two halves of the same sectors in the same round.
+  uint32_t pair;
+  int pair_hi;
 };
 constexpr size_t kDpTableWords = 3 * 2048;     // uint32 per permutation
 constexpr size_t kDpPhaseEntries = 2048 + 2048;  // double2 per segment (low + two block tables)
