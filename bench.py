@@ -304,7 +304,8 @@ HBM_PEAK_GBS = 6678.2  # measured copy bandwidth (read + write) of a GB300
 # dram__bytes_read.sum + dram__bytes_write.sum of one k_batch launch of the default workload,
 # from one ncu capture of that launch, keyed by a hash of the kernel's sources: once the
 # kernel changes the key no longer matches and traffic is null.
-KBATCH_TRAFFIC = {"fa0046678f00f781": 373.54e6 + 519.86e6}
+KBATCH_TRAFFIC = {"fa0046678f00f781": 373.54e6 + 519.86e6,
+                  "69036a9ca5c72f5d": 373.48e6 + 519.67e6}
 KBATCH_SOURCES = ("k_batch.cu", "svqe_internal.cuh", "svqe_types.h", "launch.h")
 
 

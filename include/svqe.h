@@ -322,7 +322,12 @@ sv_status sv_batch_adam_dev(sv_batch* b, double* theta_dev, double lr, int32_t n
  * (Algorithm 1's loop with a fixed step) and returns its final theta and the energies before
  * each update.  A request's results do not depend on which other requests shared its launches.
  * serial = 1 runs one request at a time, with no batching (the one-circuit-at-a-time baseline).
- * Zero fields take defaults: 4 GiB, 4096, 1, 8.  The server reserves a device arena of
+ * Large requests of at least heavy_qubits qubits (default 20) fill the GPU by themselves, so
+ * at most max_active_heavy of them (default 2) run at once; the other large-request slots stay
+ * free for mid-size requests, whose many short launches then overlap the heavy ones.  The
+ * batched launches and mid-size requests run on streams of the device's greatest priority,
+ * heavy requests on its least, so that the block scheduler starts short work first.
+ * Zero fields take defaults: 4 GiB, 4096, 1, 8, 2, 20.  The server reserves a device arena of
  * min(hbm_budget_bytes, 6 GiB) for small requests at creation; a large request gets its own
  * buffers when admitted, and keeps them idle after it finishes for the next request of the same
  * qubit count (at most max_active_large idle sets), so that steady-state admission and
@@ -335,6 +340,8 @@ typedef struct {
   int32_t steps_per_tick;
   int32_t max_active_large;
   int32_t serial;
+  int32_t max_active_heavy;
+  int32_t heavy_qubits;
 } sv_server_config;
 
 /* Times are seconds since the server was created. */

@@ -3,11 +3,17 @@
 // Requests are independent VQE optimisations (Sec. 4.1, Eq. 7).  A scheduler thread:
 //   * admits queued requests in arrival order while their device footprint fits the budget
 //     (a request that cannot fit yet is skipped unless it has waited long enough to block the
-//     ones behind it, so large requests are not starved);
+//     ones behind it, so large requests are not starved of memory; one that only waits for a
+//     slot of its kind is skipped);
+//   * runs at most max_active_heavy requests of heavy_qubits or more at once: each fills the
+//     GPU by itself, so more of them would only compete for it, while their slots serve
+//     mid-size requests whose short launches overlap them;
 //   * keeps small requests (n <= SV_BATCH_MAX_QUBITS) resident in one device arena and advances
 //     all of them by up to steps_per_tick gradient steps per launch of the persistent batched
 //     kernel (per-instance step counts, steps and trajectory offsets);
-//   * runs large requests on their own context and stream, concurrently with those launches;
+//   * runs large requests on their own context and stream, concurrently with those launches
+//     (batched launches and mid-size requests on the device's greatest stream priority, heavy
+//     requests on its least, so that the block scheduler starts short work first);
 //   * detects completion with events, copies results back and frees the request's memory.
 // A finished large request's context (state buffers, stream, Hamiltonian buffers, completion
 // event and pinned result buffer) is kept idle for the next request of the same qubit count:
@@ -129,6 +135,8 @@ struct Req {
   cudaEvent_t ev = nullptr;
   double* pin = nullptr;
   size_t pin_cap = 0;
+  cudaStream_t stream = nullptr;  // the context's stream (the server creates and destroys it)
+  bool heavy = false;             // n >= heavy_qubits
 };
 
 // The device resources of a finished large request, kept for the next request of width n.
@@ -140,6 +148,7 @@ struct Idle {
   cudaEvent_t ev = nullptr;
   double* pin = nullptr;
   size_t pin_cap = 0;
+  cudaStream_t stream = nullptr;
 };
 
 // Byte layout of a small request's arena block.
@@ -210,6 +219,7 @@ struct sv_server {
   uint64_t used = 0;
   std::deque<Idle> idle;     // oldest first
   uint64_t idle_bytes = 0;
+  int prio_hi = 0, prio_lo = 0;  // greatest and least stream priorities of the device
 };
 
 namespace {
@@ -305,6 +315,7 @@ void finish(sv_server* s, Req& r, int state, sv_status st, const char* msg) {
 void free_idle(Idle& d) {
   if (d.ham) sv_ham_free(d.ham);
   if (d.ctx) sv_destroy(d.ctx);
+  if (d.stream) cudaStreamDestroy(d.stream);
   if (d.ev) cudaEventDestroy(d.ev);
   if (d.pin) cudaFreeHost(d.pin);
   d = Idle{};
@@ -340,15 +351,18 @@ void release(sv_server* s, Req& r) {
     d.ev = r.ev;
     d.pin = r.pin;
     d.pin_cap = r.pin_cap;
+    d.stream = r.stream;
     s->idle.push_back(d);
     s->idle_bytes += d.bytes;
     r.ctx = nullptr;
     r.ham = nullptr;
     r.ev = nullptr;
     r.pin = nullptr;
+    r.stream = nullptr;
   }
   if (r.ham) { sv_ham_free(r.ham); r.ham = nullptr; }
   if (r.ctx) { sv_destroy(r.ctx); r.ctx = nullptr; }
+  if (r.stream) { cudaStreamDestroy(r.stream); r.stream = nullptr; }
   if (r.ev) { cudaEventDestroy(r.ev); r.ev = nullptr; }
   if (r.pin) { cudaFreeHost(r.pin); r.pin = nullptr; }
   if (r.state != Q_QUEUED) s->used -= r.footprint;
@@ -371,18 +385,25 @@ sv_status start_large(sv_server* s, Req& r) {
     r.ev = it->ev;
     r.pin = it->pin;
     r.pin_cap = it->pin_cap;
+    r.stream = it->stream;
     s->idle_bytes -= it->bytes;
     s->idle.erase(it);
     break;
   }
   sv_status st;
-  if (!r.ctx && (st = sv_create(&r.ctx, r.n, nullptr)) != SV_OK) return st;
+  cudaError_t e;
+  if (!r.ctx) {
+    // heavy requests on the least stream priority, mid-size ones on the greatest
+    if ((e = cudaStreamCreateWithPriority(&r.stream, cudaStreamNonBlocking,
+                                          r.heavy ? s->prio_lo : s->prio_hi)) != cudaSuccess)
+      return fail_cuda("request stream", e);
+    if ((st = sv_create(&r.ctx, r.n, r.stream)) != SV_OK) return st;
+  }
   if ((st = sv_init_reference(r.ctx, r.ref)) != SV_OK) return st;
   sv_paulisum ps{r.n, (int32_t)r.hcoef.size(), r.hx.data(), r.hz.data(), r.hcoef.data()};
   if ((st = r.ham ? ham_reload(r.ctx, r.ham, &ps) : sv_ham_upload(r.ctx, &ps, &r.ham)) != SV_OK)
     return st;
   const size_t pin_n = (size_t)r.hc.n_params + (size_t)std::max(1, r.steps);
-  cudaError_t e;
   if (r.pin_cap < pin_n) {
     if (r.pin) cudaFreeHost(r.pin);
     r.pin = nullptr;
@@ -402,35 +423,45 @@ sv_status start_large(sv_server* s, Req& r) {
 
 // Admit queued requests that fit (lock held).
 void admit(sv_server* s) {
-  int running_small = 0, running_large = 0;
+  int running_small = 0, running_large = 0, running_heavy = 0;
   for (auto& kv : s->reqs) {
     if (kv.second->state != Q_RUNNING) continue;
     (kv.second->small ? running_small : running_large)++;
+    running_heavy += kv.second->heavy;
   }
   const double t = now_since(s->t0);
   for (auto it = s->queue.begin(); it != s->queue.end();) {
     auto rp = s->reqs[*it];
     Req& r = *rp;
     if (s->cfg.serial && running_small + running_large > 0) break;
-    bool slot = r.small ? running_small < s->cfg.max_active_small
-                        : running_large < s->cfg.max_active_large;
+    const bool slot = r.small ? running_small < s->cfg.max_active_small
+                              : running_large < s->cfg.max_active_large &&
+                                    (!r.heavy || running_heavy < s->cfg.max_active_heavy);
+    // A request waiting for a slot of its own kind holds back no other kind: only requests of
+    // that kind could take the slot, and they come after it in this loop anyway.
+    if (!slot) {
+      ++it;
+      continue;
+    }
     // an idle context of this width is taken over with the bytes it already holds
     uint64_t mine = 0;
-    if (slot && !r.small)
+    if (!r.small)
       for (const Idle& d : s->idle)
         if (d.n == r.n) {
           mine = d.bytes;
           break;
         }
     const uint64_t need = r.footprint > mine ? r.footprint - mine : 0;
-    if (slot) evict_idle(s, need, r.small ? -1 : r.n);
-    bool fits = slot && s->used + s->idle_bytes + need <= s->cfg.hbm_budget_bytes;
+    evict_idle(s, need, r.small ? -1 : r.n);
+    bool fits = s->used + s->idle_bytes + need <= s->cfg.hbm_budget_bytes;
     if (fits && r.small) {
       r.block = s->alloc.alloc((int64_t)r.footprint);
       fits = r.block >= 0;
     }
     if (!fits) {
-      if (t - r.t_submit > kStarveSeconds) break;  // stop here: let this one go first
+      // the budget is shared: a request that has waited long enough for room stops later
+      // requests from taking it first
+      if (t - r.t_submit > kStarveSeconds) break;
       ++it;
       continue;
     }
@@ -449,6 +480,7 @@ void admit(sv_server* s) {
       continue;
     }
     (r.small ? running_small : running_large)++;
+    running_heavy += r.heavy;
   }
 }
 
@@ -615,7 +647,13 @@ sv_status sv_server_create(const sv_server_config* cfg, sv_server** out) {
   if (s->cfg.max_active_small <= 0) s->cfg.max_active_small = 4096;
   if (s->cfg.steps_per_tick <= 0) s->cfg.steps_per_tick = 1;
   if (s->cfg.max_active_large <= 0) s->cfg.max_active_large = 8;
-  if (s->cfg.serial) { s->cfg.max_active_small = 1; s->cfg.max_active_large = 1; }
+  if (s->cfg.max_active_heavy <= 0) s->cfg.max_active_heavy = 2;
+  if (s->cfg.heavy_qubits <= 0) s->cfg.heavy_qubits = 20;
+  if (s->cfg.serial) {
+    s->cfg.max_active_small = 1;
+    s->cfg.max_active_large = 1;
+    s->cfg.max_active_heavy = 1;
+  }
   s->t0 = std::chrono::steady_clock::now();
   cudaGetDevice(&s->device);
   // The arena holds every resident small request (its int32 offsets cap it at 6 GiB).  Large
@@ -626,7 +664,9 @@ sv_status sv_server_create(const sv_server_config* cfg, sv_server** out) {
   int grid = 0;
   if ((e = batch_prepare(12, &grid)) != cudaSuccess) { delete s; return fail_cuda("batch setup", e); }
   s->grid = grid;
-  if ((e = cudaStreamCreateWithFlags(&s->bstream, cudaStreamNonBlocking)) != cudaSuccess ||
+  if ((e = cudaDeviceGetStreamPriorityRange(&s->prio_lo, &s->prio_hi)) != cudaSuccess ||
+      (e = cudaStreamCreateWithPriority(&s->bstream, cudaStreamNonBlocking, s->prio_hi)) !=
+          cudaSuccess ||
       (e = cudaStreamCreateWithFlags(&s->ustream, cudaStreamNonBlocking)) != cudaSuccess ||
       (e = cudaEventCreateWithFlags(&s->bev, cudaEventDisableTiming)) != cudaSuccess ||
       (e = cudaMalloc((void**)&s->arena, s->arena_bytes)) != cudaSuccess ||
@@ -659,6 +699,7 @@ sv_status sv_server_submit(sv_server* s, const sv_instance* inst, const double* 
   if (st != SV_OK) return st;
   r.n = r.hc.n;
   r.small = r.n <= SV_BATCH_MAX_QUBITS;
+  r.heavy = !r.small && r.n >= s->cfg.heavy_qubits;
   st = lower_ham(&inst->ham, r.n, r.small ? SV_BATCH_MAX_QUBITS : 14, r.hh);
   if (st != SV_OK) return st;
   if (inst->ref >= (1ull << r.n)) { set_error("reference index out of range"); return SV_EINVAL; }

@@ -481,7 +481,8 @@ class Batch:
 class _ServerConfig(ctypes.Structure):
     _fields_ = [("hbm_budget_bytes", ctypes.c_uint64), ("max_active_small", ctypes.c_int32),
                 ("steps_per_tick", ctypes.c_int32), ("max_active_large", ctypes.c_int32),
-                ("serial", ctypes.c_int32)]
+                ("serial", ctypes.c_int32), ("max_active_heavy", ctypes.c_int32),
+                ("heavy_qubits", ctypes.c_int32)]
 
 
 class RequestInfo(ctypes.Structure):
@@ -504,10 +505,11 @@ class Server:
     """The continuous-batching request loop (sv_server_*)."""
 
     def __init__(self, hbm_budget_bytes=0, max_active_small=0, steps_per_tick=0,
-                 max_active_large=0, serial=False):
+                 max_active_large=0, serial=False, max_active_heavy=0, heavy_qubits=0):
         self._s = ctypes.c_void_p()
         cfg = _ServerConfig(int(hbm_budget_bytes), int(max_active_small), int(steps_per_tick),
-                            int(max_active_large), 1 if serial else 0)
+                            int(max_active_large), 1 if serial else 0, int(max_active_heavy),
+                            int(heavy_qubits))
         _check(lib().sv_server_create(ctypes.byref(cfg), ctypes.byref(self._s)))
         self._meta = {}
 

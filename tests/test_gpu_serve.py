@@ -129,3 +129,25 @@ def test_idle_contexts_are_reused_and_evicted_within_the_budget():
     st = srv.stats()
     assert st.completed == len(reqs) and st.peak_bytes_in_use <= budget
     srv.close()
+
+
+def test_heavy_requests_respect_their_quota():
+    """With heavy_qubits = 14 and max_active_heavy = 1, the 14-qubit requests run one at a
+    time while 13-qubit and batched requests run beside them; every result is bit for bit the
+    serial server's."""
+    reqs = [dict(W.hea_instance(14, 2, 40, s), steps=3, lr=0.02) for s in (11, 12, 13)]
+    reqs += [dict(W.hea_instance(13, 2, 40, s), steps=3, lr=0.02) for s in (21, 22)]
+    reqs += [dict(W.hea_instance(8, 2, 40, s), steps=3, lr=0.02) for s in (31, 32)]
+    srv = svqe.Server(max_active_large=4, max_active_heavy=1, heavy_qubits=14)
+    ids = [srv.submit(r, r["steps"], r["lr"]) for r in reqs]
+    out = [srv.wait(i, 120000) for i in ids]
+    srv.close()
+    heavy = sorted((o[2].admit_s, o[2].done_s) for o in out if o[2].n_qubits == 14)
+    for (a0, d0), (a1, d1) in zip(heavy, heavy[1:]):
+        assert a1 >= d0  # admitted only after the previous heavy request finished
+    for r, (th, es, info) in zip(reqs, out):
+        assert info.status == 0
+        one = svqe.Server(serial=True)
+        th0, es0, _ = one.wait(one.submit(r, r["steps"], r["lr"]), 120000)
+        one.close()
+        assert np.array_equal(th, th0) and np.array_equal(es, es0), r["name"]
