@@ -151,3 +151,36 @@ def test_heavy_requests_respect_their_quota():
         th0, es0, _ = one.wait(one.submit(r, r["steps"], r["lr"]), 120000)
         one.close()
         assert np.array_equal(th, th0) and np.array_equal(es, es0), r["name"]
+
+
+def test_bench_stream_sampled_against_the_oracle():
+    """The serving benchmark's own seeded stream (60 requests, n = 4-24, 20 steps each),
+    submitted at once to a default server.  Sampled requests of 4-13 qubits are replayed
+    step by step with the oracle's gradient (energy before every update, final theta); the
+    24-qubit request matches the serial server bit for bit and its first energy matches the
+    oracle."""
+    reqs = W.serve_stream(60, 1.0, seed=1005)
+    srv = svqe.Server(hbm_budget_bytes=64 << 30, steps_per_tick=2)
+    ids = [srv.submit(r, r["steps"], r["lr"]) for r in reqs]
+    out = [srv.wait(i, 600000) for i in ids]
+    srv.close()
+    ns = [r["circuit"]["n"] for r in reqs]
+    sample = []
+    for n in (4, 5, 7, 10, 13):
+        sample.append(ns.index(n))
+    for k in sample:
+        r, (th, es, info) = reqs[k], out[k]
+        assert info.status == 0
+        theta = np.array(r["theta"], dtype=np.float64)
+        for t in range(r["steps"]):
+            e0, g0 = oracle.energy_grad(r, theta)
+            assert_energy(es[t], e0, r["ham"], f"{r['name']} step {t}")
+            theta = theta - r["lr"] * g0
+        assert_grad((np.asarray(r["theta"]) - th) / r["lr"],
+                    (np.asarray(r["theta"]) - theta) / r["lr"], r["ham"], r["name"])
+    big = max(range(len(reqs)), key=lambda i: ns[i])
+    one = svqe.Server(serial=True)
+    th0, es0, _ = one.wait(one.submit(reqs[big], reqs[big]["steps"], reqs[big]["lr"]), 600000)
+    one.close()
+    assert np.array_equal(out[big][0], th0) and np.array_equal(out[big][1], es0)
+    assert_energy(out[big][1][0], oracle.energy(reqs[big]), reqs[big]["ham"], reqs[big]["name"])
