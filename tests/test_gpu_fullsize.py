@@ -40,12 +40,11 @@ def test_batch_of_4096_sampled_against_oracle():
     for i, inst in enumerate(insts):
         assert np.isfinite(e[i]) and abs(e[i]) <= l1(inst["ham"]) * (1 + 1e-12)
     sample = []
-    for n in range(4, 13):
+    for n in range(4, 13):  # per qubit count: the first, a middle and the costliest instance
         idx = [i for i, it in enumerate(insts) if it["circuit"]["n"] == n]
-        sample.append(idx[0])
-        if n == 12:  # the costliest 12-qubit instance too
-            sample.append(max(idx, key=lambda i: len(insts[i]["circuit"]["types"]) *
-                              len(insts[i]["ham"]["coeff"])))
+        costliest = max(idx, key=lambda i: len(insts[i]["circuit"]["types"]) *
+                        len(insts[i]["ham"]["coeff"]))
+        sample += sorted({idx[0], idx[len(idx) // 2], costliest})
     for i in sample:
         inst = insts[i]
         e0, g0 = oracle.energy_grad(inst)
